@@ -1,0 +1,152 @@
+"""Independent pins for the oracle: brute force, closed forms, combinatorial counts.
+
+Nothing here shares code with oracle/ or with the CUDA library.  Each routine
+computes the match set or its size from the problem definition (paper Section
+2.1) by a different route than the oracle's depth-first search.
+"""
+from __future__ import annotations
+
+import itertools
+from math import comb
+
+import numpy as np
+
+BIG = np.iinfo(np.int64).max
+
+
+def edge_order(t):
+    """Edge ids: rank by (t, input index)."""
+    return sorted(range(len(t)), key=lambda i: (int(t[i]), i))
+
+
+def brute_force(src, dst, t, edges, delta, gaps=None, elabel=None, nlabel=None,
+                edge_labels=None, node_labels=None):
+    """Every k-subset of edges in id order, tested against conditions 1-5 of the definition.
+
+    Returns the sorted list of matches (tuples of edge ids) -- exhaustive, so
+    only for tiny graphs (C(m, k) subsets).
+    """
+    k = len(edges)
+    order = edge_order(t)
+    S = [int(src[i]) for i in order]
+    D = [int(dst[i]) for i in order]
+    T = [int(t[i]) for i in order]
+    EL = None if edge_labels is None else [int(edge_labels[i]) for i in order]
+    gaps = [BIG] * (k - 1) if gaps is None else [BIG if g is None else int(g) for g in gaps]
+    out = []
+    m = len(order)
+    for combo in itertools.combinations(range(m), k):
+        ts = [T[e] for e in combo]
+        if any(ts[i] >= ts[i + 1] for i in range(k - 1)):
+            continue                                     # strictly increasing in time
+        if ts[-1] - ts[0] > delta:
+            continue                                     # span <= delta
+        if any(ts[i + 1] - ts[i] > gaps[i] for i in range(k - 1)):
+            continue                                     # per-gap bound
+        phi = {}
+        ok = True
+        for i, e in enumerate(combo):
+            x, y = edges[i]
+            for mn, gn in ((x, S[e]), (y, D[e])):
+                if phi.setdefault(mn, gn) != gn:
+                    ok = False
+        if not ok or len(set(phi.values())) != len(phi):
+            continue                                     # a consistent, injective phi
+        if elabel is not None and any(elabel[i] >= 0 and (EL is None or EL[e] != elabel[i])
+                                      for i, e in enumerate(combo)):
+            continue
+        if nlabel is not None and any(nlabel[mn] >= 0 and (node_labels is None or node_labels[gn] != nlabel[mn])
+                                      for mn, gn in phi.items()):
+            continue
+        out.append(combo)
+    return out
+
+
+# ------------------------------------------------------- two-edge closed forms
+
+def _pairs_in_window(a, b, lim):
+    """#{(i, j): a_i < b_j <= a_i + lim} for sorted int64 arrays a, b."""
+    if len(a) == 0 or len(b) == 0:
+        return 0
+    a = np.asarray(a, np.int64); b = np.asarray(b, np.int64)
+    hi = np.where(a > BIG - lim, BIG, a + lim)
+    return int((np.searchsorted(b, hi, side="right") - np.searchsorted(b, a, side="right")).sum())
+
+
+def _lists(src, dst, t):
+    """Time lists per directed pair, per node (out / in), self-loops dropped."""
+    pair, out_t, in_t = {}, {}, {}
+    for s, d, tt in zip(src.tolist(), dst.tolist(), t.tolist()):
+        if s == d:
+            continue
+        pair.setdefault((s, d), []).append(tt)
+        out_t.setdefault(s, []).append(tt)
+        in_t.setdefault(d, []).append(tt)
+    f = lambda dct: {k: np.sort(np.asarray(v, np.int64)) for k, v in dct.items()}
+    return f(pair), f(out_t), f(in_t)
+
+
+def two_edge_counts(src, dst, t, delta, gap=BIG):
+    """Counts of the five 2-edge motifs from per-pair / per-node sorted time lists.
+
+    With L = min(delta, gap), each motif is a count of ordered edge pairs
+    (e1, e2) with t1 < t2 <= t1 + L and the right endpoint pattern:
+      pingpong  (a,b),(b,a)   pairs of opposite directions on one node pair
+      repeat    (a,b),(a,b)   pairs on one directed pair
+      path      (a,b),(b,c)   in-edge then out-edge of b, minus c == a (pingpong)
+      outstar   (a,b),(a,c)   out-edge pairs of a, minus b == c (repeat)
+      instar    (b,a),(c,a)   in-edge pairs of a, minus b == c (repeat)
+    """
+    L = min(int(delta), int(gap))
+    pair, out_t, in_t = _lists(np.asarray(src), np.asarray(dst), np.asarray(t))
+    pingpong = sum(_pairs_in_window(v, pair.get((d, s), ()), L) for (s, d), v in pair.items())
+    repeat = sum(_pairs_in_window(v, v, L) for v in pair.values())
+    through = sum(_pairs_in_window(in_t.get(b, ()), out_t.get(b, ()), L) for b in set(in_t) | set(out_t))
+    fan_out = sum(_pairs_in_window(v, v, L) for v in out_t.values())
+    fan_in = sum(_pairs_in_window(v, v, L) for v in in_t.values())
+    return {"pingpong": pingpong, "repeat": repeat, "path": through - pingpong,
+            "outstar": fan_out - repeat, "instar": fan_in - repeat}
+
+
+TWO_EDGE_MOTIFS = {"pingpong": [(0, 1), (1, 0)], "repeat": [(0, 1), (0, 1)],
+                   "path": [(0, 1), (1, 2)], "outstar": [(0, 1), (0, 2)],
+                   "instar": [(1, 0), (2, 0)]}
+
+
+# ---------------------------------------------------- combinatorial families
+
+def pattern_subsequences(seq, pattern):
+    """Number of index-increasing subsequences of seq equal to pattern (DP)."""
+    dp = [0] * (len(pattern) + 1)
+    dp[0] = 1
+    for s in seq:
+        for j in range(len(pattern) - 1, -1, -1):
+            if pattern[j] == s:
+                dp[j + 1] += dp[j]
+    return dp[-1]
+
+
+def triangle_train(n):
+    """3n edges cycling a->b, b->c, c->a at t = 1..3n (nodes 0, 1, 2)."""
+    kinds = [(0, 1), (1, 2), (2, 0)]
+    src = np.array([kinds[i % 3][0] for i in range(3 * n)], np.int32)
+    dst = np.array([kinds[i % 3][1] for i in range(3 * n)], np.int32)
+    t = np.arange(1, 3 * n + 1, dtype=np.int64)
+    return src, dst, t
+
+
+def triangle_train_count(n):
+    """Temporal 3-cycles in triangle_train(n) with unbounded delta: any rotation of the
+    edge-type pattern (0,1,2) as a subsequence of the type sequence."""
+    seq = [i % 3 for i in range(3 * n)]
+    return sum(pattern_subsequences(seq, [r % 3, (r + 1) % 3, (r + 2) % 3]) for r in range(3))
+
+
+def star_burst(d):
+    """d out-edges of node 0 to leaves 1..d at times 1..d."""
+    return (np.zeros(d, np.int32), np.arange(1, d + 1, dtype=np.int32), np.arange(1, d + 1, dtype=np.int64))
+
+
+def star_burst_count(d, k):
+    """Out-star with k leaves: any k of the d edges, in time order, has k distinct leaves."""
+    return comb(d, k)
