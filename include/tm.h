@@ -1,0 +1,235 @@
+/*
+ * tm.h -- C ABI of the GB300 temporal-motif mining library (libtmgb300.so).
+ *
+ * Problem (paper Section 2.1): a temporal graph is a set of directed edges
+ * (u, v, t); a motif is k edges (x_i -> y_i) over motif nodes, matched in
+ * strictly increasing time with first-to-last span <= delta, optional per-gap
+ * bounds t_{i+1} - t_i <= gap_i (fine-grained delta-temporal motif) and
+ * optional label equalities on edges and nodes (Section 5.4.1).  Matches are
+ * isomorphic: motif nodes map injectively to graph nodes.  Output is a count
+ * or the list of matches (Section 2.1, "two flavors of output").
+ *
+ * Conventions for every call:
+ *   - Every call returns tm_status; no C++ exception crosses this boundary.
+ *   - On an error status, outputs are left untouched, except TM_E_TRUNCATED
+ *     (non-fatal, see tm_enumerate).
+ *   - "device pointer" means memory of the graph's CUDA device (cudaMalloc,
+ *     a torch CUDA tensor's data_ptr, ...); "host pointer" means pageable or
+ *     pinned host memory.  Caller-owned buffers stay caller-owned.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that return host-visible results synchronise that stream
+ *     before returning.
+ *   - Edge ids: edges are ranked by (t, input index); edge id = rank.  Every
+ *     edge id the library reports refers to this order (tm_graph_edge_perm
+ *     maps it back to input positions).
+ *   - Limits: n_edges < 2^31 - 1, n_nodes < 2^31 - 1, timestamps >= 0
+ *     (int64 seconds or any unit), k <= 8 motif edges, <= 8 motif nodes.
+ */
+#ifndef TM_H
+#define TM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TM_OK = 0,
+    TM_E_INVALID = 1,    /* bad argument, graph or motif */
+    TM_E_OOM = 2,        /* device allocation failed */
+    TM_E_TRUNCATED = 3,  /* non-fatal: enumeration hit its cap; total is exact */
+    TM_E_TIMEOUT = 4,    /* a bounded device wait ran out (result discarded) */
+    TM_E_CUDA = 5,       /* CUDA runtime error */
+    TM_E_BUSY = 6,       /* serve poll: request not finished yet */
+    TM_E_ADMISSION = 7   /* serve: request can never fit the memory budget */
+} tm_status;
+
+#define TM_MAX_EDGES 8
+#define TM_MAX_NODES 8
+
+/* Input edge list (paper Section 2.2: a chronologically ordered temporal edge
+ * list; here any order is accepted and the library sorts it).
+ *   src, dst : int32[n_edges], node ids in [0, n_nodes)
+ *   t        : int64[n_edges], >= 0
+ *   elabel   : uint8[n_edges] or NULL     (edge labels)
+ *   nlabel   : uint8[n_nodes] or NULL     (node labels)
+ *   on_device: 0 = all pointers are host pointers, 1 = device pointers.
+ * The library copies what it needs; the caller may free these after load. */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_edges;
+    const int32_t* src;
+    const int32_t* dst;
+    const int64_t* t;
+    const uint8_t* elabel;
+    const uint8_t* nlabel;
+    int32_t on_device;
+} tm_edges;
+
+/* Motif query (Section 2.1 definitions; Section 4.3 query constraints).
+ *   k          : motif edges, 1..8, listed in temporal order
+ *   n_nodes    : motif nodes, 2..8; every node must appear in some edge
+ *   esrc/edst  : x_i, y_i of motif edge i, x_i != y_i
+ *   delta      : t(e_{k-1}) - t(e_0) <= delta, delta >= 0 (inclusive)
+ *   gap[i]     : t(e_{i+1}) - t(e_i) <= gap[i]; INT64_MAX = unconstrained
+ *   elabel[i]  : required label of edge i, -1 = any (needs graph elabel)
+ *   nlabel[j]  : required label of motif node j, -1 = any (needs graph nlabel)
+ * Edge times within a match are strictly increasing; graph self-loops never
+ * match (motif edges join distinct nodes). */
+typedef struct {
+    int32_t k;
+    int32_t n_nodes;
+    uint8_t esrc[TM_MAX_EDGES];
+    uint8_t edst[TM_MAX_EDGES];
+    int64_t delta;
+    int64_t gap[TM_MAX_EDGES - 1];
+    int16_t elabel[TM_MAX_EDGES];
+    int16_t nlabel[TM_MAX_NODES];
+} tm_motif;
+
+/* Execution knobs for one query shape (see tm_autotune).
+ *   warps_per_block : 2..16
+ *   chunk_roots     : root edges a warp claims at a time (multiple of 32)
+ *   split_depth     : deepest search level whose candidate range may be
+ *                     donated to idle warps (0 = only root-level windows ...
+ *                     k-2); -1 disables donation
+ *   split_min       : donate only when more than this many candidates remain */
+typedef struct {
+    int32_t warps_per_block;
+    int32_t chunk_roots;
+    int32_t split_depth;
+    int32_t split_min;
+} tm_tuning;
+
+/* Algorithm-independent work of one query: used as the numerator of the
+ * bandwidth roofline.  nodes[i] = partial matches of i edges that locate a
+ * window for edge i; entries[i] = candidates in those windows; probe_sectors
+ * = sum over located windows of ceil(log2(list length + 1)). */
+typedef struct {
+    uint64_t roots;
+    uint64_t nodes[TM_MAX_EDGES];
+    uint64_t entries[TM_MAX_EDGES];
+    uint64_t probe_sectors;
+    uint64_t matches;
+} tm_work;
+
+typedef struct tm_graph tm_graph;
+typedef struct tm_query tm_query;
+typedef struct tm_server tm_server;
+
+/* Build the device-resident graph (paper Section 4.2 data loader; Section 2.2
+ * layout): stable sort by (t, input index), then per-node out- and in-lists of
+ * (neighbour, edge id, t) in time order.  Runs on `device`, ordered on
+ * `stream`; returns after the build has finished.  *out is library-owned. */
+tm_status tm_graph_load(const tm_edges* edges, int device, void* stream, tm_graph** out);
+
+/* Release a graph and its device memory.  NULL is accepted. */
+tm_status tm_graph_free(tm_graph* g);
+
+/* Sizes of a loaded graph (any pointer may be NULL). */
+tm_status tm_graph_info(const tm_graph* g, int64_t* n_nodes, int64_t* n_edges, uint64_t* device_bytes);
+
+/* Edge id -> input index.  out_perm: int64[n_edges], host pointer. */
+tm_status tm_graph_edge_perm(const tm_graph* g, int64_t* out_perm);
+
+/* Validate a motif against a graph and build its search plan (Section 5.1.2:
+ * per-level candidate source, mapped-node checks and constraints).  Returns
+ * TM_E_INVALID for a malformed motif or label constraints the graph cannot
+ * evaluate.  The query owns its scratch memory: one query must not run on two
+ * streams at the same time. */
+tm_status tm_query_compile(const tm_graph* g, const tm_motif* motif, tm_query** out);
+tm_status tm_query_free(tm_query* q);
+
+/* Override / read the execution knobs of a query. */
+tm_status tm_query_set_tuning(tm_query* q, const tm_tuning* tuning);
+tm_status tm_query_get_tuning(const tm_query* q, tm_tuning* tuning);
+
+/* Count matches (Section 2.1; search of Algorithm 1 rooted at every edge).
+ *   total        : host pointer, receives the exact count
+ *   per_root_dev : device pointer uint64[n_edges] or NULL; entry r receives the
+ *                  number of matches whose first edge is edge id r
+ * Synchronises the stream. */
+tm_status tm_count(tm_graph* g, tm_query* q, void* stream, uint64_t* total, uint64_t* per_root_dev);
+
+/* Count only matches whose first edge id lies in [root_begin, root_end)
+ * (one shard of the root space; Section 5.3.1 partitions roots by time).
+ * per_root_dev, if given, has root_end - root_begin entries. */
+tm_status tm_count_roots(tm_graph* g, tm_query* q, int64_t root_begin, int64_t root_end,
+                         void* stream, uint64_t* total, uint64_t* per_root_dev);
+
+/* Enumerate matches (Section 2.1 enumeration flavour, with the user-given
+ * match limit of Section 4.3).
+ *   match_dev : device pointer int32[cap * k]; row j = the k edge ids of one
+ *               match in motif-edge order
+ *   cap       : rows available
+ * Rows are the lexicographically smallest min(cap, total) matches, in
+ * lexicographic order of (e_0, ..., e_{k-1}).  *total is always exact.
+ * Returns TM_E_TRUNCATED (non-fatal) when total > cap, with *n_written = cap.
+ * Synchronises the stream. */
+tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_t* match_dev, uint64_t cap,
+                       uint64_t* n_written, uint64_t* total);
+
+/* Count nq queries in one persistent launch (replayed from a captured CUDA
+ * graph).  totals: host pointer uint64[nq].  Queries may differ in size,
+ * shape, delta and constraints.  Synchronises the stream. */
+tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, void* stream, uint64_t* totals);
+
+/* Pick tm_tuning for this query's shape by timing candidate settings on the
+ * resident graph; the choice is cached per shape in the graph and applied to
+ * q.  tuned (nullable, host) receives it. */
+tm_status tm_autotune(tm_graph* g, tm_query* q, void* stream, tm_tuning* tuned);
+
+/* Measure the algorithm-independent work counters of a query (host pointer). */
+tm_status tm_query_work(tm_graph* g, tm_query* q, void* stream, tm_work* out);
+
+/* ------------------------------------------------------------- serving --
+ * A request loop over one resident graph: submitted queries are admitted
+ * while their memory (match buffer + per-request scratch) fits the budget,
+ * batched into persistent search launches on several streams, and completed
+ * asynchronously.  Requests that arrive while others run are admitted as
+ * streams and memory free up (continuous batching). */
+typedef struct {
+    uint64_t mem_budget_bytes;   /* device bytes for match buffers + scratch (0 = 4 GiB) */
+    int32_t streams;             /* concurrent batches in flight (0 = 4) */
+    int32_t max_batch;           /* queries per launched batch (0 = 64) */
+} tm_serve_cfg;
+
+typedef struct {
+    tm_status status;            /* TM_OK or TM_E_TRUNCATED on success */
+    uint64_t total;              /* exact match count */
+    uint64_t n_written;          /* rows in matches (enumerate requests) */
+    const int32_t* matches_dev;  /* device pointer, int32[n_written * k]; valid until release */
+    int32_t k;
+    double submit_to_done_ms;    /* host wall time from submit to completion */
+} tm_result;
+
+tm_status tm_serve_start(tm_graph* g, const tm_serve_cfg* cfg, tm_server** out);
+
+/* Queue a request.  The query must stay alive until its result is released;
+ * enumerate = 1 requests up to cap matches (cap >= 1).  *ticket identifies it.
+ * TM_E_ADMISSION if the request alone exceeds the memory budget.  Thread-safe. */
+tm_status tm_serve_submit(tm_server* s, tm_query* q, int enumerate, uint64_t cap, uint64_t* ticket);
+
+/* TM_E_BUSY while the request runs; TM_OK with *out filled when finished.
+ * Thread-safe. */
+tm_status tm_serve_poll(tm_server* s, uint64_t ticket, tm_result* out);
+
+/* Block until the request finishes (bounded by timeout_ms; TM_E_TIMEOUT after). */
+tm_status tm_serve_wait(tm_server* s, uint64_t ticket, int64_t timeout_ms, tm_result* out);
+
+/* Free a finished request's match buffer and bookkeeping. */
+tm_status tm_result_release(tm_server* s, uint64_t ticket);
+
+/* Drain in-flight work, stop the loop and free the server. */
+tm_status tm_serve_stop(tm_server* s);
+
+/* Static description of a status code. */
+const char* tm_status_str(tm_status s);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* tm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,594 @@
+// C ABI: query compilation (the per-level plan), count, enumerate, batched
+// count (CUDA-graph replay), work counters, autotuning, status strings.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "tm_internal.cuh"
+
+namespace tmg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+tm_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TM_E_OOM : TM_E_CUDA;
+}
+
+// ---------------------------------------------------------------- the plan
+
+uint64_t plan_shape_hash(const tm_motif* m) {
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&](uint64_t x) { h = (h ^ x) * 1099511628211ULL; };
+    mix((uint64_t)m->k);
+    mix((uint64_t)m->n_nodes);
+    for (int i = 0; i < m->k; ++i) {
+        mix(m->esrc[i]);
+        mix(m->edst[i]);
+        mix((uint64_t)(m->elabel[i] >= 0));
+        if (i + 1 < m->k) mix((uint64_t)(m->gap[i] != INT64_MAX));
+    }
+    for (int j = 0; j < m->n_nodes; ++j) mix((uint64_t)(m->nlabel[j] >= 0));
+    return h;
+}
+
+// Per-level plan of a motif (paper Section 5.1.2): motif nodes get slots in
+// the order they are first bound; level i reads the candidate list of an
+// already-mapped endpoint (out-list of x_i, in-list of y_i, the shorter of the
+// two when both are mapped, or the whole edge list when neither is), and only
+// the slots bound so far are compared against a new node.
+tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
+    if (!m) { set_error("null motif"); return TM_E_INVALID; }
+    const int k = m->k, nn = m->n_nodes;
+    if (k < 1 || k > TM_MAX_EDGES) { set_error("k must be in [1, 8]"); return TM_E_INVALID; }
+    if (nn < 2 || nn > TM_MAX_NODES) { set_error("n_nodes must be in [2, 8]"); return TM_E_INVALID; }
+    if (m->delta < 0) { set_error("delta must be >= 0"); return TM_E_INVALID; }
+    bool used[TM_MAX_NODES] = {false};
+    for (int i = 0; i < k; ++i) {
+        if (m->esrc[i] >= nn || m->edst[i] >= nn) { set_error("motif node id >= n_nodes"); return TM_E_INVALID; }
+        if (m->esrc[i] == m->edst[i]) { set_error("motif self-loop"); return TM_E_INVALID; }
+        used[m->esrc[i]] = used[m->edst[i]] = true;
+        if (m->elabel[i] < -1 || m->elabel[i] > 255) { set_error("edge label out of range"); return TM_E_INVALID; }
+        if (m->elabel[i] >= 0 && g && !g->v.elabel && g->v.m > 0) { set_error("edge label constraint on a graph without edge labels"); return TM_E_INVALID; }
+        if (i + 1 < k && m->gap[i] < 0) { set_error("gap must be >= 0"); return TM_E_INVALID; }
+    }
+    for (int j = 0; j < nn; ++j) {
+        if (!used[j]) { set_error("motif node not used by any edge"); return TM_E_INVALID; }
+        if (m->nlabel[j] < -1 || m->nlabel[j] > 255) { set_error("node label out of range"); return TM_E_INVALID; }
+        if (m->nlabel[j] >= 0 && g && !g->v.nlabel && g->v.n > 0) { set_error("node label constraint on a graph without node labels"); return TM_E_INVALID; }
+    }
+    Plan p;
+    memset(&p, 0, sizeof p);
+    p.k = k;
+    p.n_nodes = nn;
+    p.delta = m->delta;
+    p.elabel0 = m->elabel[0];
+    p.nl_x0 = m->nlabel[m->esrc[0]];
+    p.nl_y0 = m->nlabel[m->edst[0]];
+    int slot[TM_MAX_NODES];
+    for (int j = 0; j < TM_MAX_NODES; ++j) slot[j] = -1;
+    slot[m->esrc[0]] = 0;
+    slot[m->edst[0]] = 1;
+    int nb = 2;
+    int off_c = 0, off_f = 0;
+    for (int i = 1; i < k; ++i) {
+        LevelPlan& lp = p.lv[i];
+        const int x = m->esrc[i], y = m->edst[i];
+        lp.nb = (int8_t)nb;
+        lp.elabel = m->elabel[i];
+        lp.gap = m->gap[i - 1];
+        lp.nl0 = lp.nl1 = -1;
+        lp.a = lp.b = -1;
+        if (slot[x] >= 0 && slot[y] >= 0) {
+            lp.kind = CLOSE; lp.a = (int8_t)slot[x]; lp.b = (int8_t)slot[y];
+        } else if (slot[x] >= 0) {
+            lp.kind = EXT_OUT; lp.a = (int8_t)slot[x]; slot[y] = nb++; lp.nl0 = m->nlabel[y];
+        } else if (slot[y] >= 0) {
+            lp.kind = EXT_IN; lp.a = (int8_t)slot[y]; slot[x] = nb++; lp.nl0 = m->nlabel[x];
+        } else {
+            lp.kind = FREE; slot[x] = nb++; slot[y] = nb++; lp.nl0 = m->nlabel[x]; lp.nl1 = m->nlabel[y];
+        }
+        lp.frame_off = off_c;
+        lp.frame_off_fill = off_f;
+        off_c += frame_bytes(lp.nb, i, false);
+        off_f += frame_bytes(lp.nb, i, true);
+    }
+    p.warp_smem = std::max(16, (off_c + 15) & ~15);
+    p.warp_smem_fill = std::max(16, (off_f + 15) & ~15);
+    p.tune.warps_per_block = 4;
+    p.tune.chunk_roots = 256;
+    p.tune.split_depth = k >= 3 ? 1 : (k == 2 ? 0 : -1);
+    p.tune.split_min = 256;
+    p.shape_hash = plan_shape_hash(m);
+    *out = p;
+    return TM_OK;
+}
+
+// ------------------------------------------------------------- scratch
+
+static tm_status dev_alloc(void** p, size_t bytes) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc failed for search scratch");
+        return TM_E_OOM;
+    }
+    return TM_OK;
+}
+
+tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len, uint64_t chunks, uint64_t task_cap) {
+    s->device = device;
+    if (nq > s->qcap) {
+        if (s->head) cudaFree(s->head);
+        if (s->stage) cudaFreeHost(s->stage);
+        s->head = nullptr; s->stage = nullptr; s->qcap = 0;
+        size_t bytes = s->head_bytes(nq);
+        tm_status st = dev_alloc((void**)&s->head, bytes);
+        if (st != TM_OK) return st;
+        if (cudaHostAlloc((void**)&s->stage, bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaHostAlloc failed");
+            return TM_E_OOM;
+        }
+        memset(s->stage, 0, bytes);
+        s->qcap = nq;
+    }
+    if (counters_len > s->counters_len) {
+        if (s->counters) cudaFree(s->counters);
+        if (s->counters_host) cudaFreeHost(s->counters_host);
+        s->counters = nullptr; s->counters_host = nullptr; s->counters_len = 0;
+        tm_status st = dev_alloc((void**)&s->counters, counters_len * 8);
+        if (st != TM_OK) return st;
+        if (cudaHostAlloc((void**)&s->counters_host, counters_len * 8, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaHostAlloc failed");
+            return TM_E_OOM;
+        }
+        s->counters_len = counters_len;
+    }
+    if (task_cap > s->task_cap) {
+        if (s->tasks) cudaFree(s->tasks);
+        if (s->ready) cudaFree(s->ready);
+        s->tasks = nullptr; s->ready = nullptr; s->task_cap = 0;
+        tm_status st = dev_alloc((void**)&s->tasks, task_cap * sizeof(Task));
+        if (st != TM_OK) return st;
+        st = dev_alloc((void**)&s->ready, task_cap);
+        if (st != TM_OK) return st;
+        s->task_cap = task_cap;
+    }
+    if (chunks > s->chunk_cap) {
+        if (s->chunk_cnt) cudaFree(s->chunk_cnt);
+        if (s->scan_tmp) cudaFree(s->scan_tmp);
+        s->chunk_cnt = nullptr; s->scan_tmp = nullptr; s->chunk_cap = 0;
+        tm_status st = dev_alloc((void**)&s->chunk_cnt, (chunks + 1) * 8);
+        if (st != TM_OK) return st;
+        s->scan_tmp_bytes = scan_temp_bytes(chunks + 1);
+        st = dev_alloc(&s->scan_tmp, s->scan_tmp_bytes);
+        if (st != TM_OK) return st;
+        s->chunk_cap = chunks;
+    }
+    return TM_OK;
+}
+
+void scratch_free(Scratch* s) {
+    if (s->head) cudaFree(s->head);
+    if (s->stage) cudaFreeHost(s->stage);
+    if (s->tasks) cudaFree(s->tasks);
+    if (s->ready) cudaFree(s->ready);
+    if (s->counters) cudaFree(s->counters);
+    if (s->counters_host) cudaFreeHost(s->counters_host);
+    if (s->chunk_cnt) cudaFree(s->chunk_cnt);
+    if (s->scan_tmp) cudaFree(s->scan_tmp);
+    *s = Scratch();
+}
+
+constexpr uint64_t DEFAULT_TASK_CAP = 1u << 18;   // 16 MiB of 64-byte tasks
+
+uint64_t n_chunks(uint64_t roots, int chunk_roots) { return (roots + (uint64_t)chunk_roots - 1) / (uint64_t)chunk_roots; }
+
+}  // namespace tmg
+
+using namespace tmg;
+
+struct tm_query {
+    tm_graph* g = nullptr;
+    tm_motif motif{};
+    Plan plan{};
+    bool explicit_tuning = false;
+    Scratch scratch;
+};
+
+namespace tmg {
+
+// Apply the graph's cached tuning for this query's shape, unless set explicitly.
+static void apply_cached_tuning(tm_graph* g, tm_query* q) {
+    if (q->explicit_tuning) return;
+    TuneKey key{q->plan.shape_hash, 0};
+    int64_t d = q->plan.delta;
+    while (d > 0) { key.dbucket++; d >>= 1; }
+    std::lock_guard<std::mutex> lk(g->tune_mu);
+    auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) q->plan.tune = it->second;
+}
+
+void query_plan(tm_query* q, Plan* out) {
+    apply_cached_tuning(q->g, q);
+    *out = q->plan;
+}
+
+// Stage and run one single-query count (optionally with per-root, per-chunk
+// or work outputs).  Leaves results in scratch counters; does not sync.
+static tm_status run_count(tm_graph* g, tm_query* q, uint64_t rb, uint64_t re, cudaStream_t st,
+                           unsigned long long* per_root, bool chunk_counts, bool work, int grid_override = 0) {
+    Scratch& s = q->scratch;
+    const int cr = q->plan.tune.chunk_roots;
+    uint64_t nch = n_chunks(re - rb, cr);
+    tm_status r = scratch_reserve(&s, g->device, 1, 1 + (2 + 2 * TM_MAX_EDGES + 1), chunk_counts ? nch : 0,
+                                  DEFAULT_TASK_CAP);
+    if (r != TM_OK) return r;
+    Ctrl* c = s.ctrl_stage();
+    memset(c, 0, sizeof(Ctrl));
+    c->total_chunks = nch;
+    QueryDev* qd = s.qdev_stage();
+    memset(qd, 0, sizeof(QueryDev));
+    qd->plan = q->plan;
+    qd->root_begin = rb;
+    qd->root_end = re;
+    qd->n_chunks = nch;
+    qd->chunk_base = 0;
+    qd->total = s.counters;
+    qd->per_root = per_root;
+    qd->chunk_cnt = chunk_counts ? s.chunk_cnt : nullptr;
+    qd->work = work ? s.counters + 1 : nullptr;
+    TM_CUDA(cudaMemcpyAsync(s.head, s.stage, s.head_bytes(1), cudaMemcpyHostToDevice, st));
+    TM_CUDA(cudaMemsetAsync(s.counters, 0, s.counters_len * 8, st));
+    TM_CUDA(cudaMemsetAsync(s.ready, 0, s.task_cap, st));
+    if (per_root && re > rb) TM_CUDA(cudaMemsetAsync(per_root, 0, (re - rb) * 8, st));
+    if (chunk_counts) TM_CUDA(cudaMemsetAsync(s.chunk_cnt, 0, (nch + 1) * 8, st));
+    return launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block, &s, st,
+                         grid_override, work);
+}
+
+static tm_status read_back(Scratch& s, cudaStream_t st, uint64_t n_counters) {
+    TM_CUDA(cudaMemcpyAsync(s.counters_host, s.counters, n_counters * 8, cudaMemcpyDeviceToHost, st));
+    TM_CUDA(cudaMemcpyAsync(s.stage, s.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    TM_CUDA(cudaStreamSynchronize(st));
+    if (s.ctrl_stage()->err) {
+        set_error("a bounded device wait timed out");
+        return TM_E_TIMEOUT;
+    }
+    return TM_OK;
+}
+
+}  // namespace tmg
+
+// ------------------------------------------------------------------- ABI
+
+extern "C" tm_status tm_query_compile(const tm_graph* g, const tm_motif* m, tm_query** out) {
+    if (!g || !m || !out) { set_error("null argument"); return TM_E_INVALID; }
+    Plan p;
+    tm_status s = build_plan(g, m, &p);
+    if (s != TM_OK) return s;
+    tm_query* q = new tm_query();
+    q->g = const_cast<tm_graph*>(g);
+    q->motif = *m;
+    q->plan = p;
+    *out = q;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_query_free(tm_query* q) {
+    if (!q) return TM_OK;
+    cudaSetDevice(q->g->device);
+    scratch_free(&q->scratch);
+    delete q;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_query_set_tuning(tm_query* q, const tm_tuning* t) {
+    if (!q || !t) { set_error("null argument"); return TM_E_INVALID; }
+    if (t->warps_per_block < 1 || t->warps_per_block > 16 || t->chunk_roots < 32 || (t->chunk_roots % 32) != 0 ||
+        t->split_min < 0 || t->split_depth < -1 || t->split_depth > TM_MAX_EDGES) {
+        set_error("tuning out of range");
+        return TM_E_INVALID;
+    }
+    q->plan.tune = *t;
+    q->explicit_tuning = true;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_query_get_tuning(const tm_query* q, tm_tuning* t) {
+    if (!q || !t) { set_error("null argument"); return TM_E_INVALID; }
+    *t = q->plan.tune;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_count_roots(tm_graph* g, tm_query* q, int64_t rb, int64_t re, void* stream, uint64_t* total,
+                                    uint64_t* per_root_dev) {
+    if (!g || !q || !total || q->g != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
+    if (rb < 0 || re < rb || re > g->v.m) { set_error("root range out of [0, n_edges]"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(g->device));
+    apply_cached_tuning(g, q);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (re == rb) {
+        *total = 0;
+        return TM_OK;
+    }
+    tm_status s = run_count(g, q, (uint64_t)rb, (uint64_t)re, st, (unsigned long long*)per_root_dev, false, false);
+    if (s != TM_OK) return s;
+    s = read_back(q->scratch, st, 1);
+    if (s != TM_OK) return s;
+    *total = q->scratch.counters_host[0];
+    return TM_OK;
+}
+
+extern "C" tm_status tm_count(tm_graph* g, tm_query* q, void* stream, uint64_t* total, uint64_t* per_root_dev) {
+    if (!g) { set_error("null graph"); return TM_E_INVALID; }
+    return tm_count_roots(g, q, 0, g->v.m, stream, total, per_root_dev);
+}
+
+extern "C" tm_status tm_query_work(tm_graph* g, tm_query* q, void* stream, tm_work* out) {
+    if (!g || !q || !out || q->g != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(g->device));
+    apply_cached_tuning(g, q);
+    cudaStream_t st = (cudaStream_t)stream;
+    memset(out, 0, sizeof *out);
+    if (g->v.m == 0) return TM_OK;
+    tm_status s = run_count(g, q, 0, (uint64_t)g->v.m, st, nullptr, false, true);
+    if (s != TM_OK) return s;
+    s = read_back(q->scratch, st, 1 + sizeof(tm_work) / 8);
+    if (s != TM_OK) return s;
+    memcpy(out, q->scratch.counters_host + 1, sizeof(tm_work));
+    return TM_OK;
+}
+
+extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_t* match_dev, uint64_t cap,
+                                  uint64_t* n_written, uint64_t* total) {
+    if (!g || !q || !n_written || !total || q->g != g || (cap > 0 && !match_dev)) {
+        set_error("null or mismatched argument");
+        return TM_E_INVALID;
+    }
+    TM_CUDA(cudaSetDevice(g->device));
+    apply_cached_tuning(g, q);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t m = (uint64_t)g->v.m;
+    if (m == 0) {
+        *n_written = 0;
+        *total = 0;
+        return TM_OK;
+    }
+    // pass 1: per-chunk match counts
+    tm_status s = run_count(g, q, 0, m, st, nullptr, true, false);
+    if (s != TM_OK) return s;
+    Scratch& sc = q->scratch;
+    const uint64_t nch = n_chunks(m, q->plan.tune.chunk_roots);
+    // pass 2: chunk offsets
+    s = exclusive_scan_u64(sc.chunk_cnt, sc.chunk_cnt, nch + 1, sc.scan_tmp, st);
+    if (s != TM_OK) return s;
+    s = read_back(sc, st, 1);
+    if (s != TM_OK) return s;
+    const uint64_t tot = sc.counters_host[0];
+    const uint64_t nw = std::min(tot, cap);
+    if (nw > 0) {
+        // pass 3: fill rows in lexicographic order from each chunk's offset
+        Ctrl* c = sc.ctrl_stage();
+        memset(c, 0, sizeof(Ctrl));
+        c->total_chunks = nch;
+        QueryDev* qd = sc.qdev_stage();
+        qd->per_root = nullptr;
+        qd->chunk_cnt = nullptr;
+        qd->chunk_off = sc.chunk_cnt;
+        qd->match_out = match_dev;
+        qd->cap = cap;
+        qd->work = nullptr;
+        qd->total = sc.counters + 1;
+        TM_CUDA(cudaMemcpyAsync(sc.head, sc.stage, sc.head_bytes(1), cudaMemcpyHostToDevice, st));
+        s = launch_search(g, MODE_FILL, sc.qdev(), 1, q->plan.warp_smem_fill, q->plan.tune.warps_per_block, &sc, st);
+        if (s != TM_OK) return s;
+        TM_CUDA(cudaStreamSynchronize(st));
+    }
+    *total = tot;
+    *n_written = nw;
+    return tot > cap ? TM_E_TRUNCATED : TM_OK;
+}
+
+// ------------------------------------------------------------- batching
+
+namespace tmg {
+
+// One captured CUDA graph per batch geometry: stage -> kernel -> read back.
+struct BatchExec {
+    int nq = 0, warp_smem = 0, warps = 0;
+    Scratch scratch;
+    cudaGraphExec_t exec = nullptr;
+    ~BatchExec() {
+        if (exec) cudaGraphExecDestroy(exec);
+        scratch_free(&scratch);
+    }
+};
+
+static std::mutex g_batch_mu;
+static std::map<const tm_graph*, std::vector<std::unique_ptr<BatchExec>>> g_batches;
+
+static tm_status capture_batch(tm_graph* g, BatchExec* b, cudaStream_t st) {
+    Scratch& s = b->scratch;
+    cudaStream_t cs;
+    TM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "begin capture"); }
+    cudaMemcpyAsync(s.head, s.stage, s.head_bytes(b->nq), cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(s.counters, 0, (size_t)b->nq * 8, cs);
+    cudaMemsetAsync(s.ready, 0, s.task_cap, cs);
+    tm_status ls = launch_search(g, MODE_COUNT, s.qdev(), b->nq, b->warp_smem, b->warps, &s, cs);
+    cudaMemcpyAsync(s.counters_host, s.counters, (size_t)b->nq * 8, cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(s.stage, s.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (ls != TM_OK) { if (graph) cudaGraphDestroy(graph); return ls; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    (void)st;
+    return TM_OK;
+}
+
+}  // namespace tmg
+
+extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, void* stream, uint64_t* totals) {
+    if (!g || !qs || nq < 1 || nq > 4096 || !totals) { set_error("bad batch arguments"); return TM_E_INVALID; }
+    for (int j = 0; j < nq; ++j)
+        if (!qs[j] || qs[j]->g != g) { set_error("null or mismatched query in batch"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(g->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->v.m == 0) {
+        for (int j = 0; j < nq; ++j) totals[j] = 0;
+        return TM_OK;
+    }
+    int warp_smem = 16, warps = 0;
+    for (int j = 0; j < nq; ++j) {
+        apply_cached_tuning(g, qs[j]);
+        warp_smem = std::max(warp_smem, qs[j]->plan.warp_smem);
+        warps = std::max(warps, qs[j]->plan.tune.warps_per_block);
+    }
+    BatchExec* b = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        auto& vec = g_batches[g];
+        for (auto& p : vec)
+            if (p->nq == nq && p->warp_smem == warp_smem && p->warps == warps) { b = p.get(); break; }
+        if (!b) {
+            vec.emplace_back(new BatchExec());
+            b = vec.back().get();
+            b->nq = nq; b->warp_smem = warp_smem; b->warps = warps;
+        }
+    }
+    tm_status s = scratch_reserve(&b->scratch, g->device, nq, (uint64_t)nq, 0, DEFAULT_TASK_CAP);
+    if (s != TM_OK) return s;
+    Scratch& sc = b->scratch;
+    Ctrl* c = sc.ctrl_stage();
+    memset(c, 0, sizeof(Ctrl));
+    uint64_t base = 0;
+    for (int j = 0; j < nq; ++j) {
+        QueryDev* qd = sc.qdev_stage() + j;
+        memset(qd, 0, sizeof(QueryDev));
+        qd->plan = qs[j]->plan;
+        qd->root_begin = 0;
+        qd->root_end = (uint64_t)g->v.m;
+        qd->n_chunks = n_chunks((uint64_t)g->v.m, qs[j]->plan.tune.chunk_roots);
+        qd->chunk_base = base;
+        base += qd->n_chunks;
+        qd->total = sc.counters + j;
+    }
+    c->total_chunks = base;
+    if (!b->exec) {
+        s = capture_batch(g, b, st);
+        if (s != TM_OK) return s;
+    }
+    TM_CUDA(cudaGraphLaunch(b->exec, st));
+    TM_CUDA(cudaStreamSynchronize(st));
+    if (sc.ctrl_stage()->err) { set_error("a bounded device wait timed out"); return TM_E_TIMEOUT; }
+    for (int j = 0; j < nq; ++j) totals[j] = sc.counters_host[j];
+    return TM_OK;
+}
+
+// Release batch executables of a graph (called from tm_graph_free).
+void tmg::drop_batches(const tm_graph* g) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batches.erase(g);
+}
+
+// ------------------------------------------------------------- autotune
+
+extern "C" tm_status tm_autotune(tm_graph* g, tm_query* q, void* stream, tm_tuning* tuned) {
+    if (!g || !q || q->g != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(g->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t m = (uint64_t)g->v.m;
+    tm_tuning best = q->plan.tune;
+    if (m > 0) {
+        cudaEvent_t e0, e1;
+        TM_CUDA(cudaEventCreate(&e0));
+        TM_CUDA(cudaEventCreate(&e1));
+        auto time_cfg = [&](const tm_tuning& t, float* ms) -> tm_status {
+            q->plan.tune = t;
+            float best_ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                tm_status s = run_count(g, q, 0, m, st, nullptr, false, false);
+                if (s != TM_OK) return s;
+                cudaEventRecord(e1, st);
+                TM_CUDA(cudaEventSynchronize(e1));
+                float x = 0;
+                cudaEventElapsedTime(&x, e0, e1);
+                if (rep > 0) best_ms = std::min(best_ms, x);
+                if (x > 2000.f) { best_ms = std::min(best_ms, x); break; }
+            }
+            *ms = best_ms;
+            return TM_OK;
+        };
+        float best_ms;
+        tm_status s = time_cfg(best, &best_ms);
+        // coordinate descent over the four knobs
+        const int warps_c[] = {2, 4, 8};
+        const int chunk_c[] = {64, 256, 1024};
+        const int min_c[] = {64, 256, 2048};
+        for (int knob = 0; knob < 4 && s == TM_OK; ++knob) {
+            std::vector<tm_tuning> cands;
+            for (int i = 0; i < 3; ++i) {
+                tm_tuning t = best;
+                if (knob == 0) t.warps_per_block = warps_c[i];
+                if (knob == 1) t.chunk_roots = chunk_c[i];
+                if (knob == 2) { t.split_depth = i - 1; if (t.split_depth > q->plan.k - 2) continue; }
+                if (knob == 3) t.split_min = min_c[i];
+                cands.push_back(t);
+            }
+            for (auto& t : cands) {
+                float ms;
+                s = time_cfg(t, &ms);
+                if (s != TM_OK) break;
+                if (ms < best_ms * 0.97f) { best_ms = ms; best = t; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        TM_CUDA(cudaStreamSynchronize(st));
+        if (s != TM_OK) return s;
+        q->plan.tune = best;
+        TuneKey key{q->plan.shape_hash, 0};
+        int64_t d = q->plan.delta;
+        while (d > 0) { key.dbucket++; d >>= 1; }
+        std::lock_guard<std::mutex> lk(g->tune_mu);
+        g->tuned[key] = best;
+    }
+    q->explicit_tuning = false;
+    if (tuned) *tuned = best;
+    return TM_OK;
+}
+
+// ----------------------------------------------------------------- status
+
+extern "C" const char* tm_status_str(tm_status s) {
+    switch (s) {
+        case TM_OK: return "ok";
+        case TM_E_INVALID: return "invalid argument";
+        case TM_E_OOM: return "out of device memory";
+        case TM_E_TRUNCATED: return "truncated: enumeration cap reached";
+        case TM_E_TIMEOUT: return "bounded device wait timed out";
+        case TM_E_CUDA: return "CUDA error";
+        case TM_E_BUSY: return "busy: request not finished";
+        case TM_E_ADMISSION: return "request exceeds the serving memory budget";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,341 @@
+// Graph ingest (paper Section 4.2 data loader, Section 2.2 layout), on the GPU:
+//   1. validate ids / times and find the time range (one reduction kernel)
+//   2. stable radix sort by time with the input index as payload -> edge ids
+//      (skipped when the input is already in time order)
+//   3. gather the edge columns into edge-id order
+//   4. per direction: degree histogram + exclusive scan -> list offsets;
+//      stable radix sort of (endpoint, edge id) -> lists in time order;
+//      gather (t, neighbour) columns for the lists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "tm_internal.cuh"
+
+namespace tmg {
+
+namespace {
+
+struct Check {
+    unsigned long long tmin, tmax;
+    unsigned long long bad;       // count of out-of-range ids / negative times
+    unsigned long long descents;  // count of t[i] > t[i+1]
+};
+
+__global__ void check_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                             const int64_t* __restrict__ t, int64_t m, int64_t n, Check* out) {
+    unsigned long long tmin = ~0ULL, tmax = 0, bad = 0, desc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = src[i], d = dst[i];
+        int64_t ti = t[i];
+        if (s < 0 || s >= n || d < 0 || d >= n || ti < 0) bad++;
+        unsigned long long u = (unsigned long long)(ti < 0 ? 0 : ti);
+        tmin = min(tmin, u);
+        tmax = max(tmax, u);
+        if (i + 1 < m && t[i + 1] < ti) desc++;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        tmin = min(tmin, __shfl_down_sync(0xffffffffu, tmin, d));
+        tmax = max(tmax, __shfl_down_sync(0xffffffffu, tmax, d));
+        bad += __shfl_down_sync(0xffffffffu, bad, d);
+        desc += __shfl_down_sync(0xffffffffu, desc, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&out->tmin, tmin);
+        atomicMax(&out->tmax, tmax);
+        if (bad) atomicAdd(&out->bad, bad);
+        if (desc) atomicAdd(&out->descents, desc);
+    }
+}
+
+__global__ void time_keys_kernel(const int64_t* __restrict__ t, int64_t m, unsigned long long tmin,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = (uint64_t)t[i] - tmin;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void iota_kernel(uint32_t* __restrict__ v, int64_t m) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (uint32_t)i;
+}
+
+__global__ void gather_edges_kernel(const uint32_t* __restrict__ perm, int64_t m, const int32_t* __restrict__ src,
+                                    const int32_t* __restrict__ dst, const int64_t* __restrict__ t,
+                                    const uint8_t* __restrict__ el, int32_t* __restrict__ src_o,
+                                    int32_t* __restrict__ dst_o, int64_t* __restrict__ t_o, uint8_t* __restrict__ el_o,
+                                    int32_t* __restrict__ perm_o) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i = perm[e];
+        src_o[e] = src[i];
+        dst_o[e] = dst[i];
+        t_o[e] = t[i];
+        if (el) el_o[e] = el[i];
+        perm_o[e] = (int32_t)i;
+    }
+}
+
+__global__ void degree_kernel(const int32_t* __restrict__ node, int64_t m, unsigned long long* __restrict__ deg) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[node[e]], 1ULL);
+}
+
+__global__ void node_keys_kernel(const int32_t* __restrict__ node, int64_t m, uint32_t* __restrict__ keys,
+                                 uint32_t* __restrict__ vals) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = (uint32_t)node[e];
+        vals[e] = (uint32_t)e;
+    }
+}
+
+__global__ void offsets_kernel(const unsigned long long* __restrict__ off64, int64_t n1, uint32_t* __restrict__ off) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+        off[i] = (uint32_t)off64[i];
+}
+
+__global__ void list_columns_kernel(const uint32_t* __restrict__ eids, int64_t m, const int64_t* __restrict__ t,
+                                    const int32_t* __restrict__ other, int64_t* __restrict__ at,
+                                    int32_t* __restrict__ anbr, int32_t* __restrict__ aeid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = eids[i];
+        at[i] = t[e];
+        anbr[i] = other[e];
+        aeid[i] = (int32_t)e;
+    }
+}
+
+int bits_for(unsigned long long x) {
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+struct Pool {  // temporary device allocations freed at scope exit
+    std::vector<void*> ptrs;
+    ~Pool() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    tm_status get(T** out, size_t count) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 16)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc failed during graph build");
+            return TM_E_OOM;
+        }
+        ptrs.push_back(p);
+        *out = (T*)p;
+        return TM_OK;
+    }
+};
+
+template <typename T>
+tm_status owned(tm_graph* g, T** out, size_t count) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc failed for graph storage");
+        return TM_E_OOM;
+    }
+    g->allocs.push_back(p);
+    g->device_bytes += bytes;
+    *out = (T*)p;
+    return TM_OK;
+}
+
+#define TRY(x)                              \
+    do {                                    \
+        tm_status _s = (x);                 \
+        if (_s != TM_OK) return _s;         \
+    } while (0)
+
+int grid_for(int64_t m, int sms) {
+    int64_t g = (m + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
+}
+
+tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
+    const int64_t m = e->n_edges, n = e->n_nodes;
+    const int sms = g->num_sms;
+    Pool tmp;
+    const int32_t *src = e->src, *dst = e->dst;
+    const int64_t* t = e->t;
+    const uint8_t* el = e->elabel;
+    if (!e->on_device && m > 0) {
+        int32_t *s2, *d2;
+        int64_t* t2;
+        TRY(tmp.get(&s2, m));
+        TRY(tmp.get(&d2, m));
+        TRY(tmp.get(&t2, m));
+        TM_CUDA(cudaMemcpyAsync(s2, src, m * 4, cudaMemcpyHostToDevice, st));
+        TM_CUDA(cudaMemcpyAsync(d2, dst, m * 4, cudaMemcpyHostToDevice, st));
+        TM_CUDA(cudaMemcpyAsync(t2, t, m * 8, cudaMemcpyHostToDevice, st));
+        src = s2; dst = d2; t = t2;
+        if (el) {
+            uint8_t* e2;
+            TRY(tmp.get(&e2, m));
+            TM_CUDA(cudaMemcpyAsync(e2, el, m, cudaMemcpyHostToDevice, st));
+            el = e2;
+        }
+    }
+    GraphView& v = g->v;
+    v.n = n; v.m = m;
+    // node labels
+    if (e->nlabel) {
+        uint8_t* nl;
+        TRY(owned(g, &nl, n));
+        TM_CUDA(cudaMemcpyAsync(nl, e->nlabel, n, e->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        v.nlabel = nl;
+    }
+    // 1. validate
+    Check* chk;
+    TRY(tmp.get(&chk, 1));
+    Check init{~0ULL, 0ULL, 0ULL, 0ULL};
+    TM_CUDA(cudaMemcpyAsync(chk, &init, sizeof(Check), cudaMemcpyHostToDevice, st));
+    if (m > 0) {
+        check_kernel<<<grid_for(m, sms), 256, 0, st>>>(src, dst, t, m, n, chk);
+        TM_CUDA(cudaGetLastError());
+    }
+    Check hc;
+    TM_CUDA(cudaMemcpyAsync(&hc, chk, sizeof(Check), cudaMemcpyDeviceToHost, st));
+    TM_CUDA(cudaStreamSynchronize(st));
+    if (hc.bad) {
+        set_error("edge endpoint out of [0, n_nodes) or negative timestamp");
+        return TM_E_INVALID;
+    }
+    // 2. time order
+    uint32_t *perm_a, *perm_b;
+    TRY(tmp.get(&perm_a, m));
+    TRY(tmp.get(&perm_b, m));
+    size_t rtemp_bytes = radix_temp_bytes((uint64_t)m);
+    void* rtemp;
+    TRY(tmp.get((char**)&rtemp, rtemp_bytes));
+    if (m > 0 && hc.descents > 0) {
+        uint64_t *ka, *kb;
+        TRY(tmp.get(&ka, m));
+        TRY(tmp.get(&kb, m));
+        time_keys_kernel<<<grid_for(m, sms), 256, 0, st>>>(t, m, hc.tmin, ka, perm_a);
+        TM_CUDA(cudaGetLastError());
+        TRY(radix_sort_pairs(ka, kb, perm_a, perm_b, (uint64_t)m, bits_for(hc.tmax - hc.tmin), rtemp, rtemp_bytes, st));
+    } else if (m > 0) {
+        iota_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m);
+        TM_CUDA(cudaGetLastError());
+    }
+    // 3. edge columns in edge-id order
+    int32_t *s_o, *d_o, *p_o;
+    int64_t* t_o;
+    uint8_t* el_o = nullptr;
+    TRY(owned(g, &s_o, m));
+    TRY(owned(g, &d_o, m));
+    TRY(owned(g, &t_o, m));
+    TRY(owned(g, &p_o, m));
+    if (el) TRY(owned(g, &el_o, m));
+    if (m > 0) {
+        gather_edges_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, src, dst, t, el, s_o, d_o, t_o, el_o, p_o);
+        TM_CUDA(cudaGetLastError());
+    }
+    v.src = s_o; v.dst = d_o; v.t = t_o; v.elabel = el_o;
+    g->perm = p_o;
+    // 4. adjacency lists
+    unsigned long long* deg;
+    TRY(tmp.get(&deg, n + 1));
+    size_t stemp_bytes = scan_temp_bytes((uint64_t)(n + 1));
+    void* stemp;
+    TRY(tmp.get((char**)&stemp, stemp_bytes));
+    uint32_t *nk_a, *nk_b;
+    TRY(tmp.get(&nk_a, m));
+    TRY(tmp.get(&nk_b, m));
+    int nbits = bits_for((unsigned long long)(n > 0 ? n - 1 : 0));
+    for (int dir = 0; dir < 2; ++dir) {
+        const int32_t* key_node = dir == 0 ? s_o : d_o;
+        const int32_t* other = dir == 0 ? d_o : s_o;
+        uint32_t* off;
+        int64_t* at;
+        int32_t *anbr, *aeid;
+        TRY(owned(g, &off, n + 1));
+        TRY(owned(g, &at, m));
+        TRY(owned(g, &anbr, m));
+        TRY(owned(g, &aeid, m));
+        TM_CUDA(cudaMemsetAsync(deg, 0, (n + 1) * sizeof(unsigned long long), st));
+        if (m > 0) {
+            degree_kernel<<<grid_for(m, sms), 256, 0, st>>>(key_node, m, deg);
+            TM_CUDA(cudaGetLastError());
+        }
+        TRY(exclusive_scan_u64(deg, deg, (uint64_t)(n + 1), stemp, st));
+        offsets_kernel<<<grid_for(n + 1, sms), 256, 0, st>>>(deg, n + 1, off);
+        TM_CUDA(cudaGetLastError());
+        if (m > 0) {
+            node_keys_kernel<<<grid_for(m, sms), 256, 0, st>>>(key_node, m, nk_a, perm_a);
+            TM_CUDA(cudaGetLastError());
+            TRY(radix_sort_pairs32(nk_a, nk_b, perm_a, perm_b, (uint64_t)m, nbits, rtemp, rtemp_bytes, st));
+            list_columns_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, t_o, other, at, anbr, aeid);
+            TM_CUDA(cudaGetLastError());
+        }
+        v.off[dir] = off; v.at[dir] = at; v.anbr[dir] = anbr; v.aeid[dir] = aeid;
+    }
+    TM_CUDA(cudaStreamSynchronize(st));
+    return TM_OK;
+}
+
+}  // namespace
+
+}  // namespace tmg
+
+using namespace tmg;
+
+extern "C" tm_status tm_graph_load(const tm_edges* e, int device, void* stream, tm_graph** out) {
+    if (!e || !out) { set_error("null argument"); return TM_E_INVALID; }
+    if (e->n_edges < 0 || e->n_nodes < 0 || e->n_edges >= 0x7FFFFFFF || e->n_nodes >= 0x7FFFFFFF) {
+        set_error("n_edges / n_nodes out of range");
+        return TM_E_INVALID;
+    }
+    if (e->n_edges > 0 && (!e->src || !e->dst || !e->t || e->n_nodes < 1)) {
+        set_error("missing edge columns");
+        return TM_E_INVALID;
+    }
+    int ndev = 0;
+    TM_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) { set_error("bad device"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(device));
+    tm_graph* g = new tm_graph();
+    g->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete g; return cuda_fail(cudaGetLastError(), "props"); }
+    g->num_sms = prop.multiProcessorCount;
+    tm_status s = build(g, e, (cudaStream_t)stream);
+    if (s != TM_OK) {
+        tm_graph_free(g);
+        return s;
+    }
+    *out = g;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_graph_free(tm_graph* g) {
+    if (!g) return TM_OK;
+    cudaSetDevice(g->device);
+    drop_batches(g);
+    for (void* p : g->allocs) cudaFree(p);
+    delete g;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_graph_info(const tm_graph* g, int64_t* n_nodes, int64_t* n_edges, uint64_t* device_bytes) {
+    if (!g) { set_error("null graph"); return TM_E_INVALID; }
+    if (n_nodes) *n_nodes = g->v.n;
+    if (n_edges) *n_edges = g->v.m;
+    if (device_bytes) *device_bytes = g->device_bytes;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_graph_edge_perm(const tm_graph* g, int64_t* out_perm) {
+    if (!g || (!out_perm && g->v.m > 0)) { set_error("null argument"); return TM_E_INVALID; }
+    if (g->v.m == 0) return TM_OK;
+    TM_CUDA(cudaSetDevice(g->device));
+    std::vector<int32_t> tmp((size_t)g->v.m);
+    TM_CUDA(cudaMemcpy(tmp.data(), g->perm, g->v.m * 4, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < g->v.m; ++i) out_perm[i] = tmp[i];
+    return TM_OK;
+}

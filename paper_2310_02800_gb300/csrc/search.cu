@@ -1,0 +1,666 @@
+// Persistent warp-cooperative temporal motif search (sm_103a).
+//
+// The search is the chronological depth-first search of the paper's
+// Algorithm 1 (Section 2.2), rooted at every edge, with the per-level plan of
+// Section 5.1.2 deciding where candidates come from and which mapped nodes a
+// new node must differ from.  The GPU organisation is our own:
+//
+//  * A warp owns a stack of FRAMES, one per motif edge i >= 1.  Frame i holds
+//    up to 64 partial matches of i edges ("parents"), each with its candidate
+//    window for edge i: the entries of one time-ordered adjacency list with
+//    t in (t_prev, min(t_root + delta, t_prev + gap_{i-1})], located by a
+//    binary search for the lower end and a galloping search for the upper end
+//    (the cached candidate range of Section 5.1.1 is the window itself).
+//  * The windows of a frame are flattened: lane j of a 32-wide step takes the
+//    j-th remaining candidate across all parents, so lanes stay busy even when
+//    every individual window is short.  Survivors of a step (structure, label
+//    and injectivity checks) are compacted with __ballot_sync into the child
+//    frame, which is drained once it holds >= 32 parents or its parent frame is
+//    exhausted.  Processing frames in order keeps the emitted matches in
+//    lexicographic order of edge ids (used by enumeration).
+//  * The last motif edge is never expanded: survivors are counted with
+//    __popc(ballot) and added to per-warp accumulators; per-root / per-chunk
+//    counts use __match_any_sync groups and one atomic per group.
+//  * Load balance (sub-tree-level parallelism, Section 5.2): root edges are
+//    claimed in chunks from an atomic cursor; when warps sit idle, a warp at a
+//    shallow level donates the upper half of its remaining candidate range to
+//    a device task queue (count mode only), and idle warps pop those tasks.
+//    Every device-side wait is bounded by a global-timer deadline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "tm_internal.cuh"
+
+namespace tmg {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t INLIST = 0x80000000u;
+constexpr uint64_t WAIT_NS = 20ull * 1000 * 1000 * 1000;      // idle-wait deadline
+constexpr uint64_t READY_NS = 2ull * 1000 * 1000 * 1000;      // publish-wait deadline
+
+__device__ __forceinline__ int64_t sat_add(int64_t a, int64_t b) {
+    return (b > 0 && a > INT64_MAX - b) ? INT64_MAX : a + b;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// first index in [lo, hi) with t[idx] > x
+__device__ __forceinline__ uint32_t upper_bound_t(const int64_t* __restrict__ t, uint32_t lo, uint32_t hi, int64_t x) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(t + mid) <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// first index in [beg, hi) with t[idx] > lim, searching outward from beg
+__device__ __forceinline__ uint32_t gallop_end(const int64_t* __restrict__ t, uint32_t beg, uint32_t hi, int64_t lim) {
+    uint32_t a = beg, b = hi, step = 1;
+    while (true) {
+        uint32_t probe = a + step - 1;
+        if (probe >= hi) { b = hi; break; }
+        if (__ldg(t + probe) > lim) { b = probe; break; }
+        a = probe + 1;
+        step <<= 1;
+    }
+    return upper_bound_t(t, a, b, lim);
+}
+
+__device__ __forceinline__ uint32_t ceil_log2p1(uint32_t x) { return 32 - __clz(x); }  // ceil(log2(x+1))
+
+// ------------------------------------------------------------ frame access
+
+struct Frame {
+    char* p;
+    __device__ int64_t& tprev(int s) const { return ((int64_t*)(p + F_TPREV))[s]; }
+    __device__ int64_t& tend(int s) const { return ((int64_t*)(p + F_TEND))[s]; }
+    __device__ uint32_t& beg(int s) const { return ((uint32_t*)(p + F_BEG))[s]; }
+    __device__ uint32_t& len(int s) const { return ((uint32_t*)(p + F_LEN))[s]; }
+    __device__ uint32_t& pre(int s) const { return ((uint32_t*)(p + F_PRE))[s]; }
+    __device__ uint32_t& root(int s) const { return ((uint32_t*)(p + F_ROOT))[s]; }
+    __device__ int32_t& node(int j, int s) const { return ((int32_t*)(p + F_NODE))[j * FCAP + s]; }
+    // eids follow the nb node rows
+    __device__ int32_t& eid(int nb, int j, int s) const { return ((int32_t*)(p + F_NODE))[(nb + j) * FCAP + s]; }
+};
+
+// ------------------------------------------------------------ per-warp state
+
+// work counters, laid out like tm_work
+constexpr int W_ROOTS = 0, W_NODES = 1, W_ENTRIES = 1 + TM_MAX_EDGES, W_PROBE = 1 + 2 * TM_MAX_EDGES,
+              W_MATCH = 2 + 2 * TM_MAX_EDGES, W_LEN = 3 + 2 * TM_MAX_EDGES;
+
+struct Acc {             // per-warp accumulators for the current query
+    unsigned long long total;      // warp-uniform
+    unsigned long long w[W_LEN];   // stats launches; lane-0 values except W_PROBE (per lane)
+};
+
+template <int MODE, bool STATS>
+struct Search {
+    const GraphView& g;
+    const QueryDev* __restrict__ qs;
+    Ctrl* ctrl;
+    Task* tasks;
+    uint8_t* ready;
+    uint64_t task_cap;
+    char* wbase;              // this warp's shared block
+    int lane;
+    // current query
+    int qi;
+    const QueryDev* q;
+    int k;
+    // level cursors: lane j holds the values for level j
+    uint32_t myP, myOff, myT;
+    Acc acc;
+    // enumerate fill
+    unsigned long long out_base, out_local;
+
+    __device__ Search(const GraphView& g_, const QueryDev* qs_, Ctrl* c, Task* t, uint8_t* r, uint64_t cap, char* wb)
+        : g(g_), qs(qs_), ctrl(c), tasks(t), ready(r), task_cap(cap), wbase(wb) {
+        lane = threadIdx.x & 31;
+        qi = -1; q = nullptr; k = 0;
+        myP = myOff = myT = 0;
+        acc.total = 0;
+        if (STATS) for (int i = 0; i < W_LEN; ++i) acc.w[i] = 0;
+        out_base = out_local = 0;
+    }
+
+    __device__ uint32_t P(int l) const { return __shfl_sync(FULL, myP, l); }
+    __device__ uint32_t Off(int l) const { return __shfl_sync(FULL, myOff, l); }
+    __device__ uint32_t T(int l) const { return __shfl_sync(FULL, myT, l); }
+    __device__ void setP(int l, uint32_t v) { if (lane == l) myP = v; }
+    __device__ void setOff(int l, uint32_t v) { if (lane == l) myOff = v; }
+    __device__ void setT(int l, uint32_t v) { if (lane == l) myT = v; }
+
+    __device__ Frame frame(int i) const {
+        return Frame{wbase + (MODE == MODE_FILL ? q->plan.lv[i].frame_off_fill : q->plan.lv[i].frame_off)};
+    }
+
+    __device__ void flush() {
+        if (q == nullptr) return;
+        if (lane == 0 && acc.total) atomicAdd(q->total, acc.total);
+        if (STATS) {
+            for (int i = 0; i < W_LEN; ++i) {
+                unsigned long long v = acc.w[i];
+                for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(FULL, v, d);
+                if (lane == 0 && v && q->work) atomicAdd(q->work + i, v);
+                acc.w[i] = 0;
+            }
+        }
+        acc.total = 0;
+    }
+
+    __device__ void use_query(int j) {
+        if (j == qi) return;
+        flush();
+        qi = j;
+        q = qs + j;
+        k = q->plan.k;
+    }
+
+    // Window for motif edge `lv_i` of a (child) partial match whose slots are
+    // parent slots [0, nb) of frame `pf` at index `ps`, plus new nodes n0, n1
+    // at slots nb, nb+1.  Returns len; beg gets bit 31 for in-lists.
+    __device__ uint32_t locate(int lv_i, Frame pf, int ps, int nb, int32_t n0, int32_t n1,
+                               int64_t tprev, int64_t tend, uint32_t& beg_out) {
+        const LevelPlan& lp = q->plan.lv[lv_i];
+        auto slot = [&](int s) -> int32_t { return s < nb ? pf.node(s, ps) : (s == nb ? n0 : n1); };
+        int64_t lim = min(tend, sat_add(tprev, lp.gap));
+        const int64_t* tarr;
+        uint32_t lo, hi, flag = 0;
+        int kind = lp.kind;
+        if (kind == FREE) {
+            tarr = g.t; lo = 0; hi = (uint32_t)g.m;
+        } else {
+            int dir;
+            int32_t v;
+            if (kind == EXT_OUT) { dir = 0; v = slot(lp.a); }
+            else if (kind == EXT_IN) { dir = 1; v = slot(lp.a); }
+            else {
+                int32_t u = slot(lp.a), w = slot(lp.b);
+                uint32_t du = __ldg(g.off[0] + u + 1) - __ldg(g.off[0] + u);
+                uint32_t dw = __ldg(g.off[1] + w + 1) - __ldg(g.off[1] + w);
+                if (du <= dw) { dir = 0; v = u; } else { dir = 1; v = w; }
+            }
+            lo = __ldg(g.off[dir] + v);
+            hi = __ldg(g.off[dir] + v + 1);
+            tarr = g.at[dir];
+            flag = dir ? INLIST : 0u;
+        }
+        uint32_t b = upper_bound_t(tarr, lo, hi, tprev);
+        uint32_t e = (b < hi) ? gallop_end(tarr, b, hi, lim) : b;
+        if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi - lo);
+        beg_out = b | flag;
+        return e - b;
+    }
+
+    // Exclusive prefix of window lengths over a frame's parents; returns total.
+    __device__ uint32_t begin_frame(int i) {
+        Frame f = frame(i);
+        uint32_t np = P(i);
+        const uint32_t p0 = 2u * lane, p1 = p0 + 1u;
+        uint32_t l0 = p0 < np ? f.len(p0) : 0u;
+        uint32_t l1 = p1 < np ? f.len(p1) : 0u;
+        uint32_t s = l0 + l1, inc = s;
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t u = __shfl_up_sync(FULL, inc, d);
+            if (lane >= d) inc += u;
+        }
+        uint32_t ex = inc - s;
+        if (p0 < np) f.pre(p0) = ex;
+        if (p1 < np) f.pre(p1) = ex + l0;
+        uint32_t tot = __shfl_sync(FULL, inc, 31);
+        __syncwarp();
+        setOff(i, 0);
+        setT(i, tot);
+        return tot;
+    }
+
+    // Emit survivors of the last level (or of the root level when k == 1).
+    __device__ void emit(bool ok, uint32_t root, Frame pf, int ps, int nb, int32_t last_eid) {
+        unsigned bal = __ballot_sync(FULL, ok);
+        if (!bal) return;
+        unsigned cnt = __popc(bal);
+        if (MODE == MODE_COUNT) {
+            acc.total += cnt;
+            if (STATS && lane == 0) acc.w[W_MATCH] += cnt;
+            if (q->per_root && ok) {
+                unsigned grp = __match_any_sync(bal, root);
+                if (lane == __ffs(grp) - 1) atomicAdd(q->per_root + (root - q->root_begin), (unsigned long long)__popc(grp));
+            }
+            if (q->chunk_cnt && ok) {
+                uint32_t c = (uint32_t)((root - q->root_begin) / (uint32_t)q->plan.tune.chunk_roots);
+                unsigned grp = __match_any_sync(bal, c);
+                if (lane == __ffs(grp) - 1) atomicAdd(q->chunk_cnt + c, (unsigned long long)__popc(grp));
+            }
+        } else {
+            unsigned rank = __popc(bal & ((1u << lane) - 1u));
+            unsigned long long pos = out_base + out_local + rank;
+            if (ok && pos < q->cap) {
+                int32_t* o = q->match_out + pos * (unsigned long long)k;
+                for (int j = 0; j < k - 1; ++j) o[j] = pf.eid(nb, j, ps);
+                o[k - 1] = last_eid;
+            }
+            out_local += cnt;
+        }
+    }
+
+    // One 32-candidate step of frame i.
+    __device__ void step(int i) {
+        const LevelPlan& lp = q->plan.lv[i];
+        Frame f = frame(i);
+        const int nb = lp.nb;
+        const uint32_t np = P(i), off = Off(i), tot = T(i);
+        uint32_t idx = off + lane;
+        bool act = idx < tot;
+        int p = 0;
+        if (act) {
+            int lo = 0, hi = (int)np;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (f.pre(mid) <= idx) lo = mid; else hi = mid;
+            }
+            p = lo;
+        }
+        int32_t n0 = -1, n1 = -1, ceid = -1;
+        int64_t ct = 0;
+        bool ok = act;
+        const int kind = lp.kind;
+        const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0;
+        if (act) {
+            uint32_t bw = f.beg(p);
+            uint32_t pos = (bw & ~INLIST) + (idx - f.pre(p));
+            if (kind == FREE) {
+                ct = __ldg(g.t + pos);
+                n0 = __ldg(g.src + pos);
+                n1 = __ldg(g.dst + pos);
+                ceid = (int32_t)pos;
+                ok = n0 != n1;
+                for (int j = 0; j < nb; ++j) {
+                    int32_t x = f.node(j, p);
+                    ok &= (x != n0) && (x != n1);
+                }
+                if (lp.nl0 >= 0) ok &= g.nlabel[n0] == (uint8_t)lp.nl0;
+                if (lp.nl1 >= 0) ok &= g.nlabel[n1] == (uint8_t)lp.nl1;
+            } else {
+                int dir = (bw & INLIST) ? 1 : 0;
+                ct = __ldg(g.at[dir] + pos);
+                int32_t nbr = __ldg(g.anbr[dir] + pos);
+                if (need_eid) ceid = __ldg(g.aeid[dir] + pos);
+                if (kind == CLOSE) {
+                    ok = nbr == f.node(dir ? lp.a : lp.b, p);
+                } else {
+                    n0 = nbr;
+                    for (int j = 0; j < nb; ++j) ok &= f.node(j, p) != nbr;
+                    if (lp.nl0 >= 0) ok &= g.nlabel[nbr] == (uint8_t)lp.nl0;
+                }
+            }
+            if (lp.elabel >= 0) ok &= g.elabel[ceid] == (uint8_t)lp.elabel;
+        }
+        uint32_t root = act ? f.root(p) : 0u;
+        if (i == k - 1) {
+            emit(ok, root, f, p, nb, ceid);
+            return;
+        }
+        // expand survivors into frame i+1
+        const int nb_c = q->plan.lv[i + 1].nb;
+        uint32_t cbeg = 0, clen = 0;
+        int64_t tend = 0;
+        if (ok) {
+            tend = f.tend(p);
+            clen = locate(i + 1, f, p, nb, n0, n1, ct, tend, cbeg);
+        }
+        if (STATS) {
+            unsigned b = __ballot_sync(FULL, ok);
+            uint32_t l = ok ? clen : 0u;
+            for (int d = 16; d > 0; d >>= 1) l += __shfl_down_sync(FULL, l, d);
+            if (lane == 0) {
+                acc.w[W_NODES + (i + 1)] += __popc(b);
+                acc.w[W_ENTRIES + (i + 1)] += l;
+            }
+        }
+        bool keep = ok && clen > 0;
+        unsigned kb = __ballot_sync(FULL, keep);
+        if (!kb) return;
+        uint32_t cp = P(i + 1);
+        Frame c = frame(i + 1);
+        if (keep) {
+            int s = (int)(cp + __popc(kb & ((1u << lane) - 1u)));
+            for (int j = 0; j < nb; ++j) c.node(j, s) = f.node(j, p);
+            if (nb_c > nb) c.node(nb, s) = n0;
+            if (nb_c > nb + 1) c.node(nb + 1, s) = n1;
+            c.tprev(s) = ct;
+            c.tend(s) = tend;
+            c.beg(s) = cbeg;
+            c.len(s) = clen;
+            c.root(s) = root;
+            if (MODE == MODE_FILL) {
+                for (int j = 0; j < i; ++j) c.eid(nb_c, j, s) = f.eid(nb, j, p);
+                c.eid(nb_c, i, s) = ceid;
+            }
+        }
+        __syncwarp();
+        setP(i + 1, cp + __popc(kb));
+    }
+
+    // Donate the upper half of frame i's remaining candidates as tasks.
+    __device__ void maybe_donate(int i) {
+        const uint32_t np = P(i), off = Off(i), tot = T(i);
+        const tm_tuning& tu = q->plan.tune;
+        if (i > tu.split_depth || tot - off <= (uint32_t)tu.split_min) return;
+        int idle = 0;
+        if (lane == 0) idle = *(volatile int*)&ctrl->idle;
+        idle = __shfl_sync(FULL, idle, 0);
+        if (idle <= 0) return;
+        Frame f = frame(i);
+        uint32_t mid = off + ((tot - off) >> 1);
+        mid = (mid + 31u) & ~31u;
+        if (mid >= tot || mid <= off) return;
+        // parent containing mid
+        int lo = 0, hi = (int)np;
+        while (hi - lo > 1) {
+            int m2 = (lo + hi) >> 1;
+            if (f.pre(m2) <= mid) lo = m2; else hi = m2;
+        }
+        const int p0 = lo;
+        const int ntask = (int)np - p0;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctrl->q_reserve, (unsigned long long)ntask);
+        base = __shfl_sync(FULL, base, 0);
+        if (base + (unsigned long long)ntask > task_cap) {
+            // no room: void the reserved slots that exist and keep the work
+            for (int j = lane; j < ntask; j += 32)
+                if (base + j < task_cap) *(volatile uint8_t*)&ready[base + j] = 2;
+            return;
+        }
+        const int nb = q->plan.lv[i].nb;
+        for (int j = lane; j < ntask; j += 32) {
+            int p = p0 + j;
+            uint32_t pre = f.pre(p), len = f.len(p), bw = f.beg(p);
+            uint32_t skip = (p == p0) ? (mid - pre) : 0u;
+            Task* t = tasks + base + j;
+            t->query = (int16_t)qi;
+            t->level = (int16_t)i;
+            t->beg = bw + skip;
+            t->len = len - skip;
+            t->tprev = f.tprev(p);
+            t->tend = f.tend(p);
+            t->root = f.root(p);
+            for (int s = 0; s < nb; ++s) t->node[s] = f.node(s, p);
+        }
+        __threadfence();
+        for (int j = lane; j < ntask; j += 32) *(volatile uint8_t*)&ready[base + j] = 1;
+        __syncwarp();
+        if (lane == 0) {
+            f.len(p0) = mid - f.pre(p0);
+            atomicAdd(&ctrl->donated, (unsigned)ntask);
+        }
+        __syncwarp();
+        setP(i, (uint32_t)p0 + 1);
+        setT(i, mid);
+    }
+
+    // Drain frame `base` (and everything below it) to completion.
+    __device__ void drain(int base) {
+        begin_frame(base);
+        int lvl = base;
+        while (true) {
+            if (Off(lvl) < T(lvl)) {
+                if (MODE == MODE_COUNT) maybe_donate(lvl);
+                if (Off(lvl) < T(lvl)) {
+                    step(lvl);
+                    setOff(lvl, Off(lvl) + 32);
+                    if (lvl < k - 1 && P(lvl + 1) >= 32) { ++lvl; begin_frame(lvl); }
+                }
+                continue;
+            }
+            if (lvl < k - 1 && P(lvl + 1) > 0) { ++lvl; begin_frame(lvl); continue; }
+            setP(lvl, 0);
+            if (lvl == base) break;
+            --lvl;
+        }
+    }
+
+    // Roots [r0, r1) of the current query: level 0 of the search.
+    __device__ void roots(uint64_t r0, uint64_t r1, bool flush_at_end) {
+        const Plan& pl = q->plan;
+        for (uint64_t rb = r0; rb < r1; rb += 32) {
+            uint64_t r = rb + lane;
+            bool ok = r < r1;
+            int32_t s = 0, d = 0;
+            int64_t tt = 0;
+            if (ok) {
+                s = __ldg(g.src + r);
+                d = __ldg(g.dst + r);
+                tt = __ldg(g.t + r);
+                ok = s != d;
+                if (pl.elabel0 >= 0) ok &= g.elabel[r] == (uint8_t)pl.elabel0;
+                if (pl.nl_x0 >= 0) ok &= g.nlabel[s] == (uint8_t)pl.nl_x0;
+                if (pl.nl_y0 >= 0) ok &= g.nlabel[d] == (uint8_t)pl.nl_y0;
+            }
+            if (STATS && lane == 0) acc.w[W_ROOTS] += (r1 - rb < 32ull) ? (unsigned long long)(r1 - rb) : 32ull;
+            if (k == 1) {
+                emit(ok, (uint32_t)r, Frame{wbase}, 0, 0, (int32_t)r);
+                continue;
+            }
+            uint32_t cbeg = 0, clen = 0;
+            int64_t tend = 0;
+            if (ok) {
+                tend = sat_add(tt, pl.delta);
+                clen = locate(1, Frame{wbase}, 0, 0, s, d, tt, tend, cbeg);
+            }
+            if (STATS) {
+                unsigned b = __ballot_sync(FULL, ok);
+                uint32_t l = ok ? clen : 0u;
+                for (int dd = 16; dd > 0; dd >>= 1) l += __shfl_down_sync(FULL, l, dd);
+                if (lane == 0) {
+                    acc.w[W_NODES + 1] += __popc(b);
+                    acc.w[W_ENTRIES + 1] += l;
+                }
+            }
+            bool keep = ok && clen > 0;
+            unsigned kb = __ballot_sync(FULL, keep);
+            if (kb) {
+                uint32_t cp = P(1);
+                Frame c = frame(1);
+                if (keep) {
+                    int sl = (int)(cp + __popc(kb & ((1u << lane) - 1u)));
+                    c.node(0, sl) = s;
+                    c.node(1, sl) = d;
+                    c.tprev(sl) = tt;
+                    c.tend(sl) = tend;
+                    c.beg(sl) = cbeg;
+                    c.len(sl) = clen;
+                    c.root(sl) = (uint32_t)r;
+                    if (MODE == MODE_FILL) c.eid(2, 0, sl) = (int32_t)r;
+                }
+                __syncwarp();
+                setP(1, cp + __popc(kb));
+                if (cp + __popc(kb) >= 32) drain(1);
+            }
+        }
+        if (flush_at_end && k > 1 && P(1) > 0) drain(1);
+    }
+
+    __device__ void run_task(const Task& tk) {
+        use_query(tk.query);
+        const int i = tk.level;
+        const int nb = q->plan.lv[i].nb;
+        Frame f = frame(i);
+        if (lane == 0) {
+            f.tprev(0) = tk.tprev;
+            f.tend(0) = tk.tend;
+            f.beg(0) = tk.beg;
+            f.len(0) = tk.len;
+            f.root(0) = tk.root;
+            for (int s = 0; s < nb; ++s) f.node(s, 0) = tk.node[s];
+        }
+        __syncwarp();
+        setP(i, 1);
+        drain(i);
+    }
+
+    // Global chunk c -> query index (chunks of query j are contiguous).
+    __device__ int query_of_chunk(uint64_t c, int nq) const {
+        int lo = 0, hi = nq;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (qs[mid].chunk_base <= c) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+
+    __device__ bool try_pop(Task& out) {
+        int got = 0;
+        unsigned long long h = 0;
+        if (lane == 0) {
+            for (int attempt = 0; attempt < 64 && !got; ++attempt) {
+                h = *(volatile unsigned long long*)&ctrl->q_head;
+                unsigned long long r = *(volatile unsigned long long*)&ctrl->q_reserve;
+                if (h >= min(r, (unsigned long long)task_cap)) break;
+                if (atomicCAS(&ctrl->q_head, h, h + 1) != h) continue;
+                uint64_t t0 = now_ns();
+                uint8_t st = 0;
+                while ((st = *(volatile uint8_t*)&ready[h]) == 0) {
+                    if (now_ns() - t0 > READY_NS) { atomicMax(&ctrl->err, (unsigned)TM_E_TIMEOUT); break; }
+                    __nanosleep(64);
+                }
+                if (st == 1) got = 1;
+            }
+        }
+        got = __shfl_sync(FULL, got, 0);
+        if (!got) return false;
+        h = __shfl_sync(FULL, h, 0);
+        __threadfence();
+        const uint32_t* src = (const uint32_t*)(tasks + h);
+        uint32_t w = lane < 16 ? __ldcg(src + lane) : 0u;
+        uint32_t* dst = (uint32_t*)&out;
+        for (int j = 0; j < 16; ++j) dst[j] = __shfl_sync(FULL, w, j);
+        return true;
+    }
+
+    __device__ bool queue_empty() const {
+        unsigned long long h = *(volatile unsigned long long*)&ctrl->q_head;
+        unsigned long long r = *(volatile unsigned long long*)&ctrl->q_reserve;
+        return h >= min(r, (unsigned long long)task_cap);
+    }
+
+    __device__ void run(int nq, uint64_t total_chunks) {
+        if (MODE == MODE_COUNT && lane == 0) atomicAdd(&ctrl->busy, 1);
+        // phase 1: root chunks
+        while (true) {
+            unsigned long long c = 0;
+            if (lane == 0) c = atomicAdd(&ctrl->next_chunk, 1ULL);
+            c = __shfl_sync(FULL, c, 0);
+            if (c >= total_chunks) break;
+            int j = query_of_chunk(c, nq);
+            if (j != qi) {
+                // frames of the previous query must be empty before switching
+                if (MODE == MODE_COUNT && qi >= 0 && k > 1 && P(1) > 0) drain(1);
+                use_query(j);
+            }
+            uint64_t lc = c - q->chunk_base;
+            uint64_t cr = (uint64_t)q->plan.tune.chunk_roots;
+            uint64_t r0 = q->root_begin + lc * cr;
+            uint64_t r1 = min(q->root_end, r0 + cr);
+            if (MODE == MODE_FILL) {
+                out_base = q->chunk_off[lc];
+                out_local = 0;
+                if (out_base >= q->cap) {
+                    // offsets never decrease: skip the rest of this query's chunks
+                    unsigned long long nxt = (j + 1 < nq) ? qs[j + 1].chunk_base : total_chunks;
+                    if (lane == 0) atomicMax(&ctrl->next_chunk, nxt);
+                    continue;
+                }
+            }
+            roots(r0, r1, MODE == MODE_FILL);
+        }
+        if (MODE == MODE_COUNT && qi >= 0 && k > 1 && P(1) > 0) drain(1);
+        // phase 2 (count): help with donated subtrees until no warp holds work
+        if (MODE == MODE_COUNT) {
+            Task tk;
+            while (true) {
+                if (try_pop(tk)) { run_task(tk); continue; }
+                int leave = 0;
+                if (lane == 0) {
+                    atomicSub(&ctrl->busy, 1);
+                    atomicAdd(&ctrl->idle, 1);
+                    uint64_t t0 = now_ns();
+                    unsigned ns = 32;
+                    while (true) {
+                        int b = *(volatile int*)&ctrl->busy;
+                        __threadfence();
+                        if (!queue_empty()) { atomicAdd(&ctrl->busy, 1); break; }
+                        if (b == 0) { leave = 1; break; }
+                        if (now_ns() - t0 > WAIT_NS) { leave = 1; break; }
+                        __nanosleep(ns);
+                        if (ns < 1024) ns <<= 1;
+                    }
+                    atomicSub(&ctrl->idle, 1);
+                }
+                leave = __shfl_sync(FULL, leave, 0);
+                if (leave) break;
+            }
+        }
+        flush();
+    }
+};
+
+template <int MODE, bool STATS>
+__global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ GraphView g,
+                                                     const QueryDev* __restrict__ qs, int nq, int warp_smem,
+                                                     Ctrl* ctrl, Task* tasks, uint8_t* ready, uint64_t task_cap) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5;
+    Search<MODE, STATS> s(g, qs, ctrl, tasks, ready, task_cap, smem + (size_t)warp * warp_smem);
+    s.run(nq, ctrl->total_chunks);
+}
+
+}  // namespace
+
+LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int warps_per_block) {
+    LaunchCfg c;
+    c.warps_per_block = std::max(1, std::min(16, warps_per_block));
+    // keep the block's frames within the 227 KB of shared memory a block may use
+    while (c.warps_per_block > 1 && max_warp_smem * c.warps_per_block > 232448) c.warps_per_block--;
+    c.smem_bytes = max_warp_smem * c.warps_per_block;
+    int blocks = 0;
+    const void* fn = mode == MODE_COUNT ? (const void*)search_kernel<MODE_COUNT, false>
+                                        : (const void*)search_kernel<MODE_FILL, false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, c.warps_per_block * 32, c.smem_bytes);
+    if (blocks < 1) blocks = 1;
+    c.grid = blocks * g->num_sms;
+    return c;
+}
+
+tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, int nq, int max_warp_smem,
+                        int warps_per_block, const Scratch* s, cudaStream_t st, int grid_override, bool stats) {
+    LaunchCfg c = search_launch_cfg(g, mode, max_warp_smem, warps_per_block);
+    int grid = grid_override > 0 ? grid_override : c.grid;
+    dim3 block(c.warps_per_block * 32);
+    if (mode == MODE_COUNT) {
+        if (stats) {
+            cudaFuncSetAttribute((const void*)search_kernel<MODE_COUNT, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem_bytes);
+            search_kernel<MODE_COUNT, true><<<grid, block, c.smem_bytes, st>>>(
+                g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
+        } else {
+            search_kernel<MODE_COUNT, false><<<grid, block, c.smem_bytes, st>>>(
+                g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
+        }
+    } else {
+        search_kernel<MODE_FILL, false><<<grid, block, c.smem_bytes, st>>>(
+            g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
+    }
+    TM_CUDA(cudaGetLastError());
+    return TM_OK;
+}
+
+}  // namespace tmg

@@ -1,0 +1,389 @@
+// Serving loop: continuous batching of motif queries over one resident graph.
+//
+// A scheduler thread owns `streams` slots.  Whenever a slot is free and
+// requests are waiting, it admits them in arrival order while their device
+// memory (match buffer + per-chunk counts for enumeration) fits the budget,
+// and launches them as ONE multi-query persistent search on the slot's
+// stream: a count launch for every admitted request, then (for enumerate
+// requests) a chunk-offset scan and a multi-query fill launch.  Each slot's
+// grid is sized to its share of the GPU, so batches on different slots run
+// side by side and a request that arrives while others run starts as soon as
+// a slot frees, without waiting for the rest of the GPU.  Completion is
+// detected with CUDA events; results stay on the device until released.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#include "tm_internal.cuh"
+
+namespace tmg {
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+enum ReqState { QUEUED = 0, RUNNING = 1, DONE = 2 };
+
+struct Req {
+    uint64_t ticket = 0;
+    tm_query* q = nullptr;
+    Plan plan{};
+    int enumerate = 0;
+    uint64_t cap = 0;
+    uint64_t need = 0;          // admitted device bytes
+    ReqState state = QUEUED;
+    clk::time_point t_submit, t_done;
+    int32_t* match = nullptr;   // device rows (enumerate)
+    unsigned long long* chunk = nullptr;  // device chunk counts / offsets
+    void* scan_tmp = nullptr;
+    uint64_t nch = 0;
+    uint64_t total = 0, n_written = 0;
+    tm_status status = TM_OK;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    Scratch count_s, fill_s;    // staging + scratch of the two launches
+    std::vector<Req*> batch;
+    bool busy = false;
+};
+
+}  // namespace
+
+}  // namespace tmg
+
+using namespace tmg;
+
+struct tm_server {
+    tm_graph* g = nullptr;
+    tm_serve_cfg cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req*> pending;
+    std::map<uint64_t, std::unique_ptr<Req>> reqs;
+    uint64_t next_ticket = 1;
+    uint64_t mem_used = 0;
+    bool stop = false;
+    std::vector<Slot> slots;
+    std::thread th;
+    int grid_share = 0;
+    cudaStream_t free_st = nullptr;
+};
+
+namespace tmg {
+
+namespace {
+
+uint64_t req_bytes(const tm_graph* g, const Plan& p, int enumerate, uint64_t cap) {
+    if (!enumerate) return 0;
+    uint64_t nch = ((uint64_t)g->v.m + p.tune.chunk_roots - 1) / (uint64_t)p.tune.chunk_roots;
+    return cap * (uint64_t)p.k * 4 + (nch + 1) * 8 + scan_temp_bytes(nch + 1);
+}
+
+tm_status launch_batch(tm_server* s, Slot& sl) {
+    tm_graph* g = s->g;
+    const int nq = (int)sl.batch.size();
+    const uint64_t m = (uint64_t)g->v.m;
+    tm_status r = scratch_reserve(&sl.count_s, g->device, nq, (uint64_t)nq, 0, 1u << 18);
+    if (r != TM_OK) return r;
+    r = scratch_reserve(&sl.fill_s, g->device, nq, (uint64_t)nq, 0, 0);
+    if (r != TM_OK) return r;
+    // enumerate buffers (stream-ordered allocations: no device-wide sync)
+    for (Req* q : sl.batch) {
+        if (!q->enumerate) continue;
+        q->nch = (m + q->plan.tune.chunk_roots - 1) / (uint64_t)q->plan.tune.chunk_roots;
+        TM_CUDA(cudaMallocAsync((void**)&q->match, std::max<uint64_t>(q->cap * q->plan.k * 4, 16), sl.st));
+        TM_CUDA(cudaMallocAsync((void**)&q->chunk, (q->nch + 1) * 8, sl.st));
+        TM_CUDA(cudaMallocAsync(&q->scan_tmp, scan_temp_bytes(q->nch + 1), sl.st));
+        TM_CUDA(cudaMemsetAsync(q->chunk, 0, (q->nch + 1) * 8, sl.st));
+    }
+    // count launch over every request of the batch
+    Scratch& cs = sl.count_s;
+    Ctrl* c = cs.ctrl_stage();
+    memset(c, 0, sizeof(Ctrl));
+    uint64_t base = 0;
+    int warp_smem = 16, warps = 1;
+    for (int j = 0; j < nq; ++j) {
+        Req* q = sl.batch[j];
+        QueryDev* qd = cs.qdev_stage() + j;
+        memset(qd, 0, sizeof(QueryDev));
+        qd->plan = q->plan;
+        qd->root_begin = 0;
+        qd->root_end = m;
+        qd->n_chunks = (m + q->plan.tune.chunk_roots - 1) / (uint64_t)q->plan.tune.chunk_roots;
+        qd->chunk_base = base;
+        base += qd->n_chunks;
+        qd->total = cs.counters + j;
+        qd->chunk_cnt = q->enumerate ? q->chunk : nullptr;
+        warp_smem = std::max(warp_smem, q->plan.warp_smem);
+        warps = std::max(warps, q->plan.tune.warps_per_block);
+    }
+    c->total_chunks = base;
+    TM_CUDA(cudaMemcpyAsync(cs.head, cs.stage, cs.head_bytes(nq), cudaMemcpyHostToDevice, sl.st));
+    TM_CUDA(cudaMemsetAsync(cs.counters, 0, (size_t)nq * 8, sl.st));
+    TM_CUDA(cudaMemsetAsync(cs.ready, 0, cs.task_cap, sl.st));
+    LaunchCfg lc = search_launch_cfg(g, MODE_COUNT, warp_smem, warps);
+    int grid = std::max(1, std::min(lc.grid, s->grid_share * std::max(1, lc.grid / std::max(1, g->num_sms)) ));
+    r = launch_search(g, MODE_COUNT, cs.qdev(), nq, warp_smem, warps, &cs, sl.st, grid);
+    if (r != TM_OK) return r;
+    // fill launch over the enumerate requests
+    int ne = 0;
+    Scratch& fs = sl.fill_s;
+    Ctrl* fc = fs.ctrl_stage();
+    memset(fc, 0, sizeof(Ctrl));
+    uint64_t fbase = 0;
+    int fsmem = 16;
+    for (Req* q : sl.batch) {
+        if (!q->enumerate) continue;
+        r = exclusive_scan_u64(q->chunk, q->chunk, q->nch + 1, q->scan_tmp, sl.st);
+        if (r != TM_OK) return r;
+        QueryDev* qd = fs.qdev_stage() + ne;
+        memset(qd, 0, sizeof(QueryDev));
+        qd->plan = q->plan;
+        qd->root_begin = 0;
+        qd->root_end = m;
+        qd->n_chunks = q->nch;
+        qd->chunk_base = fbase;
+        fbase += q->nch;
+        qd->total = fs.counters + ne;
+        qd->chunk_off = q->chunk;
+        qd->match_out = q->match;
+        qd->cap = q->cap;
+        fsmem = std::max(fsmem, q->plan.warp_smem_fill);
+        ++ne;
+    }
+    if (ne > 0) {
+        fc->total_chunks = fbase;
+        TM_CUDA(cudaMemcpyAsync(fs.head, fs.stage, fs.head_bytes(ne), cudaMemcpyHostToDevice, sl.st));
+        LaunchCfg lf = search_launch_cfg(g, MODE_FILL, fsmem, warps);
+        int fgrid = std::max(1, std::min(lf.grid, s->grid_share * std::max(1, lf.grid / std::max(1, g->num_sms))));
+        r = launch_search(g, MODE_FILL, fs.qdev(), ne, fsmem, warps, &fs, sl.st, fgrid);
+        if (r != TM_OK) return r;
+    }
+    TM_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, (size_t)nq * 8, cudaMemcpyDeviceToHost, sl.st));
+    TM_CUDA(cudaMemcpyAsync(cs.stage, cs.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, sl.st));
+    for (Req* q : sl.batch) {
+        if (!q->enumerate) continue;
+        TM_CUDA(cudaFreeAsync(q->chunk, sl.st));
+        TM_CUDA(cudaFreeAsync(q->scan_tmp, sl.st));
+        q->chunk = nullptr;
+        q->scan_tmp = nullptr;
+    }
+    TM_CUDA(cudaEventRecord(sl.done, sl.st));
+    return TM_OK;
+}
+
+void finish_batch(tm_server* s, Slot& sl, tm_status launch_status) {
+    // caller holds s->mu
+    bool timeout = launch_status == TM_OK && sl.count_s.ctrl_stage()->err != 0;
+    auto now = clk::now();
+    for (size_t j = 0; j < sl.batch.size(); ++j) {
+        Req* q = sl.batch[j];
+        q->t_done = now;
+        if (launch_status != TM_OK) {
+            q->status = launch_status;
+        } else if (timeout) {
+            q->status = TM_E_TIMEOUT;
+        } else {
+            q->total = sl.count_s.counters_host[j];
+            q->n_written = q->enumerate ? std::min(q->total, q->cap) : 0;
+            q->status = (q->enumerate && q->total > q->cap) ? TM_E_TRUNCATED : TM_OK;
+        }
+        // chunk scratch was freed on the stream; the match buffer stays until release
+        uint64_t keep = q->enumerate ? q->cap * (uint64_t)q->plan.k * 4 : 0;
+        s->mem_used -= (q->need - keep);
+        q->need = keep;
+        q->state = DONE;
+    }
+    sl.batch.clear();
+    sl.busy = false;
+}
+
+void scheduler(tm_server* s) {
+    cudaSetDevice(s->g->device);
+    const int max_batch = s->cfg.max_batch;
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        // completions
+        bool any_busy = false;
+        for (Slot& sl : s->slots) {
+            if (!sl.busy) continue;
+            cudaError_t e = cudaEventQuery(sl.done);
+            if (e == cudaSuccess) {
+                finish_batch(s, sl, TM_OK);
+                s->cv_done.notify_all();
+            } else if (e != cudaErrorNotReady) {
+                cudaGetLastError();
+                finish_batch(s, sl, TM_E_CUDA);
+                s->cv_done.notify_all();
+            } else {
+                any_busy = true;
+            }
+        }
+        if (s->stop && s->pending.empty() && !any_busy) break;
+        // admissions into a free slot
+        Slot* free_slot = nullptr;
+        for (Slot& sl : s->slots)
+            if (!sl.busy) { free_slot = &sl; break; }
+        if (free_slot && !s->pending.empty()) {
+            for (auto it = s->pending.begin(); it != s->pending.end() && (int)free_slot->batch.size() < max_batch;) {
+                Req* q = *it;
+                if (s->mem_used + q->need <= s->cfg.mem_budget_bytes) {
+                    s->mem_used += q->need;
+                    q->state = RUNNING;
+                    free_slot->batch.push_back(q);
+                    it = s->pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            if (!free_slot->batch.empty()) {
+                free_slot->busy = true;
+                tm_status r = launch_batch(s, *free_slot);
+                if (r != TM_OK) {
+                    finish_batch(s, *free_slot, r);
+                    s->cv_done.notify_all();
+                }
+                continue;
+            }
+        }
+        s->cv_work.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+    }
+}
+
+}  // namespace
+
+}  // namespace tmg
+
+extern "C" tm_status tm_serve_start(tm_graph* g, const tm_serve_cfg* cfg, tm_server** out) {
+    if (!g || !out) { set_error("null argument"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(g->device));
+    tm_server* s = new tm_server();
+    s->g = g;
+    s->cfg = cfg ? *cfg : tm_serve_cfg{0, 0, 0};
+    if (s->cfg.mem_budget_bytes == 0) s->cfg.mem_budget_bytes = 4ull << 30;
+    if (s->cfg.streams <= 0) s->cfg.streams = 4;
+    if (s->cfg.streams > 32) s->cfg.streams = 32;
+    if (s->cfg.max_batch <= 0) s->cfg.max_batch = 64;
+    s->grid_share = std::max(1, g->num_sms / s->cfg.streams);
+    s->slots.resize(s->cfg.streams);
+    for (Slot& sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("stream/event creation failed");
+            delete s;
+            return TM_E_CUDA;
+        }
+    }
+    cudaStreamCreateWithFlags(&s->free_st, cudaStreamNonBlocking);
+    s->th = std::thread(scheduler, s);
+    *out = s;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_serve_submit(tm_server* s, tm_query* q, int enumerate, uint64_t cap, uint64_t* ticket) {
+    if (!s || !q || !ticket) { set_error("null argument"); return TM_E_INVALID; }
+    if (enumerate && cap < 1) { set_error("enumerate request needs cap >= 1"); return TM_E_INVALID; }
+    std::unique_ptr<Req> r(new Req());
+    // snapshot the plan (with the graph's tuning for this shape) at submit time
+    query_plan(q, &r->plan);
+    r->q = q;
+    r->enumerate = enumerate ? 1 : 0;
+    r->cap = enumerate ? cap : 0;
+    r->need = req_bytes(s->g, r->plan, r->enumerate, r->cap);
+    if (r->need > s->cfg.mem_budget_bytes) {
+        set_error("request needs more device memory than the serving budget");
+        return TM_E_ADMISSION;
+    }
+    r->t_submit = clk::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) { set_error("server stopping"); return TM_E_INVALID; }
+    r->ticket = s->next_ticket++;
+    *ticket = r->ticket;
+    s->pending.push_back(r.get());
+    s->reqs[r->ticket] = std::move(r);
+    s->cv_work.notify_one();
+    return TM_OK;
+}
+
+static void fill_result(const Req* r, tm_result* out) {
+    out->status = r->status;
+    out->total = r->total;
+    out->n_written = r->n_written;
+    out->matches_dev = r->match;
+    out->k = r->plan.k;
+    out->submit_to_done_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+}
+
+extern "C" tm_status tm_serve_poll(tm_server* s, uint64_t ticket, tm_result* out) {
+    if (!s || !out) { set_error("null argument"); return TM_E_INVALID; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("unknown ticket"); return TM_E_INVALID; }
+    if (it->second->state != DONE) return TM_E_BUSY;
+    fill_result(it->second.get(), out);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_serve_wait(tm_server* s, uint64_t ticket, int64_t timeout_ms, tm_result* out) {
+    if (!s || !out) { set_error("null argument"); return TM_E_INVALID; }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("unknown ticket"); return TM_E_INVALID; }
+    Req* r = it->second.get();
+    bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(std::max<int64_t>(0, timeout_ms)),
+                                  [&] { return r->state == DONE; });
+    if (!ok) { set_error("request still running at timeout"); return TM_E_TIMEOUT; }
+    fill_result(r, out);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_result_release(tm_server* s, uint64_t ticket) {
+    if (!s) { set_error("null argument"); return TM_E_INVALID; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("unknown ticket"); return TM_E_INVALID; }
+    Req* r = it->second.get();
+    if (r->state != DONE) { set_error("request not finished"); return TM_E_BUSY; }
+    if (r->match) {
+        cudaSetDevice(s->g->device);
+        cudaFreeAsync(r->match, s->free_st);
+        r->match = nullptr;
+    }
+    s->mem_used -= r->need;
+    s->reqs.erase(it);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_serve_stop(tm_server* s) {
+    if (!s) return TM_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->th.joinable()) s->th.join();
+    cudaSetDevice(s->g->device);
+    for (auto& kv : s->reqs)
+        if (kv.second->match) cudaFreeAsync(kv.second->match, s->free_st);
+    cudaStreamSynchronize(s->free_st);
+    for (Slot& sl : s->slots) {
+        scratch_free(&sl.count_s);
+        scratch_free(&sl.fill_s);
+        cudaEventDestroy(sl.done);
+        cudaStreamDestroy(sl.st);
+    }
+    cudaStreamDestroy(s->free_st);
+    delete s;
+    return TM_OK;
+}

@@ -1,0 +1,231 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tm.h"
+
+namespace tmg {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+tm_status cuda_fail(cudaError_t e, const char* what);
+
+#define TM_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return tmg::cuda_fail(_e, #call); \
+    } while (0)
+
+// ------------------------------------------------------------ device graph
+
+// Device-resident temporal graph (paper Section 2.2): the chronological edge
+// list plus out- and in-adjacency in time order, stored column-wise so that a
+// binary search touches only the time column and a window scan reads
+// contiguous (t, neighbour) runs.
+struct GraphView {
+    int64_t n, m;
+    const int32_t* src;       // by edge id
+    const int32_t* dst;
+    const int64_t* t;
+    const uint8_t* elabel;    // nullable
+    const uint8_t* nlabel;    // nullable
+    const uint32_t* off[2];   // [0] out, [1] in : n+1 list offsets
+    const int64_t* at[2];     // list entry time
+    const int32_t* anbr[2];   // list entry neighbour (dst for out, src for in)
+    const int32_t* aeid[2];   // list entry edge id
+};
+
+struct TuneKey {
+    uint64_t shape;     // motif structure hash
+    int dbucket;        // floor(log2(delta + 1))
+    bool operator==(const TuneKey& o) const { return shape == o.shape && dbucket == o.dbucket; }
+};
+struct TuneKeyHash {
+    size_t operator()(const TuneKey& k) const { return (size_t)(k.shape * 1315423911ULL + (uint64_t)k.dbucket); }
+};
+
+}  // namespace tmg
+
+struct tm_graph {
+    int device = 0;
+    tmg::GraphView v{};
+    std::vector<void*> allocs;     // device buffers owned by the graph
+    int32_t* perm = nullptr;       // device: edge id -> input index
+    uint64_t device_bytes = 0;
+    int num_sms = 0;
+    std::mutex tune_mu;
+    std::unordered_map<tmg::TuneKey, tm_tuning, tmg::TuneKeyHash> tuned;
+};
+
+namespace tmg {
+
+// --------------------------------------------------------------- the plan
+
+enum LevelKind : int8_t { EXT_OUT = 0, EXT_IN = 1, CLOSE = 2, FREE = 3 };
+
+// How one search level binds motif edge i (paper Section 5.1.2 "minfo"):
+// which mapped node supplies the candidate list, which mapped nodes a new
+// node must differ from, and the constraints checked on a candidate.
+struct LevelPlan {
+    int8_t kind;       // LevelKind
+    int8_t a;          // EXT_OUT: slot of x_i; EXT_IN: slot of y_i; CLOSE: slot of x_i
+    int8_t b;          // CLOSE: slot of y_i
+    int8_t nb;         // slots bound before this level
+    int16_t elabel;    // -1 = any
+    int16_t nl0;       // label of the (first) new node, -1 = any
+    int16_t nl1;       // FREE: label of the second new node (y_i)
+    int16_t pad;
+    int32_t frame_off;       // byte offset of this level's frame in a warp's shared block (count)
+    int32_t frame_off_fill;  // same, enumerate-fill layout (frames also carry edge ids)
+    int32_t pad2;
+    int64_t gap;             // t_i - t_{i-1} bound (INT64_MAX = none)
+};
+
+constexpr int FCAP = 64;          // parents per frame (two per lane)
+
+struct Plan {
+    int32_t k, n_nodes;
+    int64_t delta;
+    int16_t elabel0, nl_x0, nl_y0, pad0;
+    int32_t warp_smem;             // bytes of shared memory a warp needs (count)
+    int32_t warp_smem_fill;        // same, enumerate fill
+    tm_tuning tune;
+    uint64_t shape_hash;
+    LevelPlan lv[TM_MAX_EDGES];    // lv[i] for i = 1..k-1
+};
+
+// Frame field offsets (bytes, relative to frame start), FCAP entries each.
+//   tprev i64, tend i64, beg u32 (bit 31: in-list), len u32, pre u32, root u32,
+//   node[nb] i32, eid[i] i32 (enumerate only)
+constexpr int F_TPREV = 0;
+constexpr int F_TEND = F_TPREV + 8 * FCAP;
+constexpr int F_BEG = F_TEND + 8 * FCAP;
+constexpr int F_LEN = F_BEG + 4 * FCAP;
+constexpr int F_PRE = F_LEN + 4 * FCAP;
+constexpr int F_ROOT = F_PRE + 4 * FCAP;
+constexpr int F_NODE = F_ROOT + 4 * FCAP;
+inline int frame_bytes(int nb, int level, bool with_eids) {
+    return F_NODE + 4 * FCAP * (nb + (with_eids ? level : 0));
+}
+constexpr int WARP_HDR = 128;      // per-warp header: level cursors
+
+tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out);
+uint64_t plan_shape_hash(const tm_motif* m);
+
+// --------------------------------------------------------- device scratch
+
+// Donated search task: one partial match (its mapped nodes, times and window).
+struct Task {
+    int16_t query;
+    int16_t level;
+    uint32_t beg;        // bit 31: in-list
+    uint32_t len;
+    uint32_t root;
+    int64_t tprev;
+    int64_t tend;
+    int32_t node[TM_MAX_NODES];
+};
+static_assert(sizeof(Task) == 64, "task is one 64-byte record");
+
+// Per-launch control block.
+struct Ctrl {
+    unsigned long long total_chunks; // root chunks of all queries of the launch
+    unsigned long long next_chunk;   // root-chunk cursor
+    unsigned long long q_reserve;    // task slots reserved by donors
+    unsigned long long q_head;       // next task slot to pop
+    int busy;                        // warps holding work
+    int idle;                        // warps waiting for tasks
+    unsigned int err;                // 0 or TM_E_TIMEOUT
+    unsigned int donated;            // tasks donated (diagnostic)
+    unsigned long long pad[2];
+};
+static_assert(sizeof(Ctrl) == 64, "control block is 64 bytes");
+
+struct QueryDev {                    // one query of a launch
+    Plan plan;
+    uint64_t root_begin, root_end;
+    uint64_t n_chunks;
+    uint64_t chunk_base;             // first global chunk index of this query
+    unsigned long long* total;       // device counter
+    unsigned long long* per_root;    // nullable (indexed by root - root_begin)
+    unsigned long long* chunk_cnt;   // nullable (enumerate count pass)
+    const unsigned long long* chunk_off;  // enumerate fill: exclusive prefix of chunk_cnt
+    int32_t* match_out;              // enumerate fill
+    uint64_t cap;
+    unsigned long long* work;        // nullable: tm_work counters (2 + 2*TM_MAX_EDGES + 1)
+};
+
+// Device memory a launch uses beyond its inputs and outputs, plus the pinned
+// host staging it is initialised from.  Layout of `head` (device) and `stage`
+// (pinned host): one Ctrl, then nq QueryDev records.
+struct Scratch {
+    int device = 0;
+    char* head = nullptr;            // device: Ctrl + QueryDev[qcap]
+    char* stage = nullptr;           // pinned host mirror of head
+    int qcap = 0;
+    Task* tasks = nullptr;
+    uint8_t* ready = nullptr;
+    uint64_t task_cap = 0;
+    unsigned long long* counters = nullptr;   // device: totals, work counters
+    unsigned long long* counters_host = nullptr;  // pinned mirror
+    uint64_t counters_len = 0;
+    unsigned long long* chunk_cnt = nullptr;  // device: enumerate per-chunk counts / offsets
+    uint64_t chunk_cap = 0;
+    void* scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
+    Ctrl* ctrl() const { return (Ctrl*)head; }
+    QueryDev* qdev() const { return (QueryDev*)(head + sizeof(Ctrl)); }
+    Ctrl* ctrl_stage() const { return (Ctrl*)stage; }
+    QueryDev* qdev_stage() const { return (QueryDev*)(stage + sizeof(Ctrl)); }
+    size_t head_bytes(int nq) const { return sizeof(Ctrl) + (size_t)nq * sizeof(QueryDev); }
+};
+
+void drop_batches(const tm_graph* g);
+
+// The query's plan with the graph's cached tuning for its shape applied.
+void query_plan(tm_query* q, Plan* out);
+
+tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len, uint64_t chunks,
+                          uint64_t task_cap);
+void scratch_free(Scratch* s);
+
+enum Mode { MODE_COUNT = 0, MODE_FILL = 1 };
+
+struct LaunchCfg {
+    int warps_per_block;
+    int grid;
+    int smem_bytes;      // per block
+};
+
+// Launch the persistent search over nq queries (qdev already on the device).
+// Ctrl (incl. total_chunks) and qdev must already be initialised on the stream.
+tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, int nq,
+                        int max_warp_smem, int warps_per_block,
+                        const Scratch* s, cudaStream_t st, int grid_override = 0, bool stats = false);
+
+LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int warps_per_block);
+
+// ------------------------------------------------------------- primitives
+
+// Exclusive prefix sum of n uint64 values (in place allowed).  Needs
+// scan_temp_bytes(n) bytes of device temp.
+size_t scan_temp_bytes(uint64_t n);
+tm_status exclusive_scan_u64(const unsigned long long* in, unsigned long long* out, uint64_t n,
+                             void* temp, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+// keys/vals are double-buffered: on return *_a holds the result.
+tm_status radix_sort_pairs(uint64_t* keys_a, uint64_t* keys_b, uint32_t* vals_a, uint32_t* vals_b,
+                           uint64_t n, int bits, void* temp, size_t temp_bytes, cudaStream_t st);
+tm_status radix_sort_pairs32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b,
+                             uint64_t n, int bits, void* temp, size_t temp_bytes, cudaStream_t st);
+size_t radix_temp_bytes(uint64_t n);
+
+}  // namespace tmg
