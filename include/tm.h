@@ -174,6 +174,19 @@ tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_t* match_de
  * shape, delta and constraints.  Synchronises the stream. */
 tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, void* stream, uint64_t* totals);
 
+/* Device timing of this query's search launches.  tm_query_profile(q, 1)
+ * makes later tm_count / tm_enumerate calls record CUDA events around the
+ * search kernel (count pass) and the enumeration fill kernel on the caller's
+ * stream; tm_query_last_ms reads the last call's durations in milliseconds
+ * (fill_ms = 0 when the last call had no fill pass).  Only valid after the
+ * call has returned. */
+tm_status tm_query_profile(tm_query* q, int enable);
+tm_status tm_query_last_ms(const tm_query* q, double* search_ms, double* fill_ms);
+
+/* Number of CUDA kernels (and CUDA-graph replays) this library has launched
+ * since it was loaded, over all threads. */
+uint64_t tm_kernel_launches(void);
+
 /* Pick tm_tuning for this query's shape by timing candidate settings on the
  * resident graph; the choice is cached per shape in the graph and applied to
  * q.  tuned (nullable, host) receives it. */

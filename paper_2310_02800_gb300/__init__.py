@@ -92,9 +92,16 @@ _SIGS = [
     ("tm_serve_wait", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_Result)]),
     ("tm_result_release", ctypes.c_int, [_P, ctypes.c_uint64]),
     ("tm_serve_stop", ctypes.c_int, [_P]),
+    ("tm_query_profile", ctypes.c_int, [_P, ctypes.c_int]),
+    ("tm_query_last_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("tm_kernel_launches", ctypes.c_uint64, []),
     ("tm_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tm_last_error", ctypes.c_char_p, []),
 ]
+
+
+def kernel_launches() -> int:
+    return int(lib().tm_kernel_launches())
 
 
 def library_path() -> str:
@@ -279,6 +286,15 @@ class Query:
                                        ctypes.byref(nw), ctypes.byref(tot)), allow=(OK, E_TRUNCATED))
         return nw.value, tot.value, st == E_TRUNCATED
 
+    def profile(self, enable=True):
+        _check(lib().tm_query_profile(self._h, 1 if enable else 0))
+
+    def last_ms(self):
+        """(search kernel ms, fill kernel ms) of the last count / enumerate call."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().tm_query_last_ms(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def autotune(self, stream=None) -> dict:
         t = Tuning()
         _check(lib().tm_autotune(self.graph._h, self._h, _stream_ptr(stream), ctypes.byref(t)))
@@ -327,14 +343,17 @@ class Server:
         return Result(r.status, r.total, r.n_written, r.matches_dev or 0, r.k, r.submit_to_done_ms)
 
     def matches(self, res: Result):
-        """Copy a finished request's rows to a new int32 CUDA tensor [n_written, k]."""
+        """Copy a finished request's rows (library-owned until release) to a new int32 CUDA
+        tensor [n_written, k]."""
         import torch
-        out = torch.empty((res.n_written, res.k), dtype=torch.int32, device=f"cuda:{self.graph.device}")
-        if res.n_written:
-            L = ctypes.CDLL(None)
-            cudart = torch.cuda.cudart()
-            cudart.cudaMemcpy(out.data_ptr(), res.matches_ptr, res.n_written * res.k * 4, 3)
-        return out
+        dev = f"cuda:{self.graph.device}"
+        if not res.n_written:
+            return torch.empty((0, res.k), dtype=torch.int32, device=dev)
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (res.n_written, res.k), "typestr": "<i4",
+                                        "data": (res.matches_ptr, True), "version": 2, "strides": None}
+        return torch.as_tensor(_View(), device=dev).clone()
 
     def release(self, ticket):
         _check(lib().tm_result_release(self._h, int(ticket)))

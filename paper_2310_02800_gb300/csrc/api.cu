@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -15,6 +16,9 @@
 namespace tmg {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -204,6 +208,10 @@ struct tm_query {
     Plan plan{};
     bool explicit_tuning = false;
     Scratch scratch;
+    // optional device timing of the search launches: [0,1] count pass, [2,3] fill pass
+    bool profile = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool fill_timed = false;
 };
 
 namespace tmg {
@@ -253,8 +261,13 @@ static tm_status run_count(tm_graph* g, tm_query* q, uint64_t rb, uint64_t re, c
     TM_CUDA(cudaMemsetAsync(s.ready, 0, s.task_cap, st));
     if (per_root && re > rb) TM_CUDA(cudaMemsetAsync(per_root, 0, (re - rb) * 8, st));
     if (chunk_counts) TM_CUDA(cudaMemsetAsync(s.chunk_cnt, 0, (nch + 1) * 8, st));
-    return launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block, &s, st,
-                         grid_override, work);
+    if (q->profile) TM_CUDA(cudaEventRecord(q->ev[0], st));
+    r = launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block, &s, st,
+                      grid_override, work);
+    if (r != TM_OK) return r;
+    if (q->profile) TM_CUDA(cudaEventRecord(q->ev[1], st));
+    q->fill_timed = false;
+    return TM_OK;
 }
 
 static tm_status read_back(Scratch& s, cudaStream_t st, uint64_t n_counters) {
@@ -289,6 +302,8 @@ extern "C" tm_status tm_query_free(tm_query* q) {
     if (!q) return TM_OK;
     cudaSetDevice(q->g->device);
     scratch_free(&q->scratch);
+    for (auto& e : q->ev)
+        if (e) cudaEventDestroy(e);
     delete q;
     return TM_OK;
 }
@@ -302,6 +317,25 @@ extern "C" tm_status tm_query_set_tuning(tm_query* q, const tm_tuning* t) {
     }
     q->plan.tune = *t;
     q->explicit_tuning = true;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_query_profile(tm_query* q, int enable) {
+    if (!q) { set_error("null query"); return TM_E_INVALID; }
+    TM_CUDA(cudaSetDevice(q->g->device));
+    if (enable && !q->ev[0])
+        for (auto& e : q->ev) TM_CUDA(cudaEventCreate(&e));
+    q->profile = enable != 0;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_query_last_ms(const tm_query* q, double* search_ms, double* fill_ms) {
+    if (!q || !q->profile) { set_error("profiling not enabled on this query"); return TM_E_INVALID; }
+    float a = 0.f, b = 0.f;
+    TM_CUDA(cudaEventElapsedTime(&a, q->ev[0], q->ev[1]));
+    if (q->fill_timed) TM_CUDA(cudaEventElapsedTime(&b, q->ev[2], q->ev[3]));
+    if (search_ms) *search_ms = a;
+    if (fill_ms) *fill_ms = q->fill_timed ? b : 0.0;
     return TM_OK;
 }
 
@@ -391,8 +425,10 @@ extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_
         qd->work = nullptr;
         qd->total = sc.counters + 1;
         TM_CUDA(cudaMemcpyAsync(sc.head, sc.stage, sc.head_bytes(1), cudaMemcpyHostToDevice, st));
+        if (q->profile) TM_CUDA(cudaEventRecord(q->ev[2], st));
         s = launch_search(g, MODE_FILL, sc.qdev(), 1, q->plan.warp_smem_fill, q->plan.tune.warps_per_block, &sc, st);
         if (s != TM_OK) return s;
+        if (q->profile) { TM_CUDA(cudaEventRecord(q->ev[3], st)); q->fill_timed = true; }
         TM_CUDA(cudaStreamSynchronize(st));
     }
     *total = tot;
@@ -495,6 +531,7 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
         if (s != TM_OK) return s;
     }
     TM_CUDA(cudaGraphLaunch(b->exec, st));
+    note_launches(1);
     TM_CUDA(cudaStreamSynchronize(st));
     if (sc.ctrl_stage()->err) { set_error("a bounded device wait timed out"); return TM_E_TIMEOUT; }
     for (int j = 0; j < nq; ++j) totals[j] = sc.counters_host[j];
@@ -592,3 +629,5 @@ extern "C" const char* tm_status_str(tm_status s) {
 }
 
 extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" uint64_t tm_kernel_launches(void) { return g_launches.load(); }

@@ -196,6 +196,7 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
     TM_CUDA(cudaMemcpyAsync(chk, &init, sizeof(Check), cudaMemcpyHostToDevice, st));
     if (m > 0) {
         check_kernel<<<grid_for(m, sms), 256, 0, st>>>(src, dst, t, m, n, chk);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
     }
     Check hc;
@@ -217,10 +218,12 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
         TRY(tmp.get(&ka, m));
         TRY(tmp.get(&kb, m));
         time_keys_kernel<<<grid_for(m, sms), 256, 0, st>>>(t, m, hc.tmin, ka, perm_a);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
         TRY(radix_sort_pairs(ka, kb, perm_a, perm_b, (uint64_t)m, bits_for(hc.tmax - hc.tmin), rtemp, rtemp_bytes, st));
     } else if (m > 0) {
         iota_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
     }
     // 3. edge columns in edge-id order
@@ -234,6 +237,7 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
     if (el) TRY(owned(g, &el_o, m));
     if (m > 0) {
         gather_edges_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, src, dst, t, el, s_o, d_o, t_o, el_o, p_o);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
     }
     v.src = s_o; v.dst = d_o; v.t = t_o; v.elabel = el_o;
@@ -261,16 +265,20 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
         TM_CUDA(cudaMemsetAsync(deg, 0, (n + 1) * sizeof(unsigned long long), st));
         if (m > 0) {
             degree_kernel<<<grid_for(m, sms), 256, 0, st>>>(key_node, m, deg);
+            note_launches(1);
             TM_CUDA(cudaGetLastError());
         }
         TRY(exclusive_scan_u64(deg, deg, (uint64_t)(n + 1), stemp, st));
         offsets_kernel<<<grid_for(n + 1, sms), 256, 0, st>>>(deg, n + 1, off);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
         if (m > 0) {
             node_keys_kernel<<<grid_for(m, sms), 256, 0, st>>>(key_node, m, nk_a, perm_a);
+            note_launches(1);
             TM_CUDA(cudaGetLastError());
             TRY(radix_sort_pairs32(nk_a, nk_b, perm_a, perm_b, (uint64_t)m, nbits, rtemp, rtemp_bytes, st));
             list_columns_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, t_o, other, at, anbr, aeid);
+            note_launches(1);
             TM_CUDA(cudaGetLastError());
         }
         v.off[dir] = off; v.at[dir] = at; v.anbr[dir] = anbr; v.aeid[dir] = aeid;

@@ -117,16 +117,19 @@ tm_status exclusive_scan_u64(const unsigned long long* in, unsigned long long* o
     uint64_t nb = ceil_div(n, SCAN_TILE);
     if (nb == 1) {
         scan_down_kernel<<<1, SCAN_THREADS, 0, st>>>(in, out, n, nullptr);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
         return TM_OK;
     }
     unsigned long long* partial = (unsigned long long*)temp;
     void* rest = (char*)temp + ((nb * 8 + 255) / 256) * 256;
     scan_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, partial);
+    note_launches(1);
     TM_CUDA(cudaGetLastError());
     tm_status s = exclusive_scan_u64(partial, partial, nb, rest, st);
     if (s != TM_OK) return s;
     scan_down_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, partial);
+    note_launches(1);
     TM_CUDA(cudaGetLastError());
     return TM_OK;
 }
@@ -220,10 +223,12 @@ tm_status radix_sort_pairs_t(K* keys_a, K* keys_b, uint32_t* vals_a, uint32_t* v
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
         radix_hist_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(ki, n, shift, ntiles, counts);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
         tm_status s = exclusive_scan_u64(counts, counts, cnt, scan_tmp, st);
         if (s != TM_OK) return s;
         radix_scatter_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, ntiles, counts);
+        note_launches(1);
         TM_CUDA(cudaGetLastError());
         K* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;

@@ -651,13 +651,16 @@ tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, 
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem_bytes);
             search_kernel<MODE_COUNT, true><<<grid, block, c.smem_bytes, st>>>(
                 g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
+            note_launches(1);
         } else {
             search_kernel<MODE_COUNT, false><<<grid, block, c.smem_bytes, st>>>(
                 g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
+            note_launches(1);
         }
     } else {
         search_kernel<MODE_FILL, false><<<grid, block, c.smem_bytes, st>>>(
             g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
+        note_launches(1);
     }
     TM_CUDA(cudaGetLastError());
     return TM_OK;

@@ -15,6 +15,9 @@ namespace tmg {
 // ------------------------------------------------------------------ errors
 
 void set_error(const std::string& msg);
+
+// Kernels this library has launched (all entry points, all threads).
+void note_launches(uint64_t n);
 tm_status cuda_fail(cudaError_t e, const char* what);
 
 #define TM_CUDA(call)                                         \
