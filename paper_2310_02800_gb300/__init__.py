@@ -352,7 +352,7 @@ class Server:
 
         class _View:
             __cuda_array_interface__ = {"shape": (res.n_written, res.k), "typestr": "<i4",
-                                        "data": (res.matches_ptr, True), "version": 2, "strides": None}
+                                        "data": (res.matches_ptr, False), "version": 2, "strides": None}
         return torch.as_tensor(_View(), device=dev).clone()
 
     def release(self, ticket):
