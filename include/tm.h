@@ -195,6 +195,32 @@ tm_status tm_autotune(tm_graph* g, tm_query* q, void* stream, tm_tuning* tuned);
 /* Measure the algorithm-independent work counters of a query (host pointer). */
 tm_status tm_query_work(tm_graph* g, tm_query* q, void* stream, tm_work* out);
 
+/* Batched count that allocates nothing (the paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at query
+ * time -- code inside a pre-planned CUDA-graph or real-time loop, processes
+ * under a fixed memory cap or an allocator that forbids cudaMalloc after
+ * start-up, plug-ins whose host framework owns every allocation).
+ * Same result as tm_count_batch: the same persistent multi-query count kernel,
+ * but its scratch (control block, launch records, donated-task queue) lives in
+ * one file-scope __device__ array of TM_NOALLOC_SCRATCH_BYTES bytes that every
+ * GPU loading this library holds until the process exits; no cudaMalloc,
+ * cudaFree or other allocating call is made.
+ *   qs, nq     : compiled queries of graph g, 1 <= nq <= TM_NOALLOC_MAX_QUERIES
+ *                (TM_E_INVALID beyond that, with a message naming the limit)
+ *   totals_dev : device pointer uint64[nq], caller-owned; receives the counts
+ * At most TM_NOALLOC_TASKS donated subtrees are queued at once (further
+ * donations are kept by the donating warp; results are unchanged).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * previous call's contents; each call rewrites and clears what it uses.  Calls
+ * that overlap on the GPU (two streams, two host threads) race on the array
+ * and must be serialised by the caller.  Synchronises the stream. */
+#define TM_NOALLOC_MAX_QUERIES 64
+#define TM_NOALLOC_TASKS 4096
+#define TM_NOALLOC_SCRATCH_BYTES (320 * 1024)
+tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, int nq, void* stream, uint64_t* totals_dev);
+
 /* ------------------------------------------------------------- serving --
  * A request loop over one resident graph: submitted queries are admitted
  * while their memory (match buffer + per-request scratch) fits the budget,

@@ -84,6 +84,7 @@ _SIGS = [
     ("tm_count_roots", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _U64P, _P]),
     ("tm_enumerate", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_uint64, _U64P, _U64P]),
     ("tm_count_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    ("tm_count_batch_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     ("tm_autotune", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Tuning)]),
     ("tm_query_work", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_Work)]),
     ("tm_serve_start", ctypes.c_int, [_P, ctypes.POINTER(_ServeCfg), _PP]),
@@ -229,6 +230,13 @@ class Graph:
         out = np.zeros(len(queries), np.uint64)
         _check(lib().tm_count_batch(self._h, arr, len(queries), _stream_ptr(stream), out.ctypes.data))
         return [int(x) for x in out]
+
+    def count_batch_noalloc(self, queries, totals, stream=None):
+        """Batched count that allocates nothing: totals is a caller-owned uint64/int64 CUDA tensor
+        with len(queries) entries (at most 64 queries per call)."""
+        arr = (ctypes.c_void_p * len(queries))(*[q._h.value for q in queries])
+        _check(lib().tm_count_batch_noalloc(self._h, arr, len(queries), _stream_ptr(stream), _ptr(totals)))
+        return totals
 
     def serve(self, mem_budget_bytes=0, streams=0, max_batch=0) -> "Server":
         cfg = _ServeCfg(int(mem_budget_bytes), int(streams), int(max_batch))

@@ -227,6 +227,8 @@ static void apply_cached_tuning(tm_graph* g, tm_query* q) {
     if (it != g->tuned.end()) q->plan.tune = it->second;
 }
 
+const tm_graph* query_graph(const tm_query* q) { return q->g; }
+
 void query_plan(tm_query* q, Plan* out) {
     apply_cached_tuning(q->g, q);
     *out = q->plan;
