@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="graph size multiplier (1.0 = full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip batched / served / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", default="powerlaw_10m", choices=["powerlaw_10m", "hubskew_100m", "serve_1b"],
+    ap.add_argument("--workload", default="powerlaw_10m",
+                    choices=["powerlaw_10m", "hubskew_100m", "serve_1b", "batch64"],
                     help="powerlaw_10m: count + enumerate of 4 queries (default); hubskew_100m: count of the "
                          "labelled 5-edge path and the chorded 4-cycle; serve_1b: served Poisson traces on the "
                          "1B-edge graph")
@@ -224,6 +225,13 @@ def main():
     stream = torch.cuda.Stream()
     if args.workload == "serve_1b":
         return serve_1b(args, dev)
+    if args.workload == "batch64":
+        import synth as _s
+        g0 = _s.powerlaw_10m(scale=args.scale)
+        gg0 = tmg.Graph.from_synth(g0, device=dev, stream=stream)
+        print(json.dumps({"workload": "batch64", "config": {"graph": g0.name, "delta_range_s": [60, 86400]},
+                          "batched": batched_leg(gg0, dev, stream, dmax=86_400.0)}), flush=True)
+        return
     g, queries = workload(args.scale, args.workload)
     count_only = args.workload == "hubskew_100m"
     m = g.n_edges
@@ -303,6 +311,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "matches_per_s": matches * ws / (ms / 1000.0),
         "totals": totals,
+        "count_kernel_ms": [round(float(np.mean([k[2 * i] for k, _ in search_ms])), 4) for i in range(len(queries))],
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -354,11 +363,13 @@ def e2e_leg(args, g, queries, dev):
             "includes": "host->device upload and GPU build of the graph, 4x(count + enumerate), rows to host"}
 
 
-def batched_leg(gg, dev, stream):
-    """64-query mix: one persistent CUDA-graph launch vs 64 single-query launches."""
+def batched_leg(gg, dev, stream, dmax=3600.0):
+    """64-query mix (k in 2..6, delta log-uniform in [60, dmax]): one persistent CUDA-graph
+    launch vs 64 single-query launches.  The default dmax keeps the leg to seconds; the full
+    [60, 86400] range is --workload batch64."""
     import torch
     import synth
-    mix = synth.query_mix(64)
+    mix = synth.query_mix(64, dmax=dmax)
     qs = [gg.compile(q) for q in mix]
     with torch.cuda.stream(stream):
         want = gg.count_batch(qs, stream=stream)
@@ -377,22 +388,23 @@ def batched_leg(gg, dev, stream):
         ts = (time.perf_counter() - t0) / reps
     ok = single == want
     m = gg.n_edges
-    return {"queries": 64, "batched_ms": 1000 * tb, "sequential_ms": 1000 * ts,
+    return {"queries": 64, "delta_range_s": [60, dmax], "batched_ms": 1000 * tb, "sequential_ms": 1000 * ts,
             "batched_root_edges_per_s": 64 * m / tb, "sequential_root_edges_per_s": 64 * m / ts,
             "speedup": ts / tb, "totals_equal": ok, "matches": int(sum(want))}
 
 
-def served_leg(gg, dev, duration_s=3.0):
-    """Poisson arrivals (50 / 200 / 1000 q/s) of a 70% count / 30% enumerate mix (cap 1e6):
-    served (continuous batching) vs serial single-query execution of the same trace."""
+def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400):
+    """Poisson arrivals (50 / 200 / 1000 q/s) of a 70% count / 30% enumerate mix (cap 1e6),
+    k in 2..6, delta log-uniform in [60, dmax]: served (continuous batching) vs serial
+    single-query execution of the same trace."""
     import torch
     import synth
-    out = {}
-    mix = synth.query_mix(256, seed=synth.SEED_BASE + 5, dmax=86_400.0)
+    out = {"delta_range_s": [60, dmax]}
+    mix = synth.query_mix(256, seed=synth.SEED_BASE + 5, dmax=dmax)
     kinds = synth.draws(synth.SEED_BASE + 5, 601, 256)
     qs = [gg.compile(q) for q in mix]
     for rate in (50, 200, 1000):
-        n = max(8, int(rate * duration_s))
+        n = min(max_requests, max(8, int(rate * duration_s)))
         arr = synth.arrival_trace(rate, n, synth.SEED_BASE + 5, stream=700 + rate)
         reqs = [(float(arr[i]), i % len(qs), int(kinds[i % len(kinds)] % 10) < 3) for i in range(n)]
         srv = gg.serve(mem_budget_bytes=8 << 30, streams=4, max_batch=64)
@@ -447,7 +459,7 @@ def serve_1b(args, dev):
     gg = tmg.Graph.from_synth(g, device=dev)
     load_s = time.perf_counter() - t0
     del g
-    res = served_leg(gg, dev, duration_s=2.0)
+    res = served_leg(gg, dev, duration_s=2.0, dmax=86_400.0, max_requests=200)
     line = {"metric": "p50/p99 latency and throughput, served vs serial", "workload": gg.n_edges,
             "config": {"workload": f"powerlaw_1b x{args.scale}", "n_edges": gg.n_edges, "n_nodes": gg.n_nodes,
                        "device_bytes": gg.device_bytes, "generate_s": gen_s, "load_s": load_s},

@@ -88,12 +88,15 @@ typedef struct {
 } tm_motif;
 
 /* Execution knobs for one query shape (see tm_autotune).
- *   warps_per_block : 2..16
+ *   warps_per_block : 1..16 (reduced automatically when the block's search
+ *                     frames would not fit in shared memory)
  *   chunk_roots     : root edges a warp claims at a time (multiple of 32)
- *   split_depth     : deepest search level whose candidate range may be
- *                     donated to idle warps (0 = only root-level windows ...
- *                     k-2); -1 disables donation
- *   split_min       : donate only when more than this many candidates remain */
+ *   split_depth     : deepest search level whose remaining candidates may be
+ *                     donated to idle warps: level i holds the candidate windows
+ *                     of motif edge i (1 = the root edges' windows, up to k-1);
+ *                     0 or -1 disables donation
+ *   split_min       : a donation moves, on average, at least this many
+ *                     candidates per donated task */
 typedef struct {
     int32_t warps_per_block;
     int32_t chunk_roots;

@@ -92,12 +92,25 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
         lp.gap = m->gap[i - 1];
         lp.nl0 = lp.nl1 = -1;
         lp.a = lp.b = -1;
+        lp.nx_a = lp.nx_b = NX_NONE;
+        // lists of an endpoint of edge i-1 start right after that edge's time:
+        // their window start is read from the graph's successor index
+        const int px = slot[m->esrc[i - 1]], py = slot[m->edst[i - 1]];
+        auto succ = [&](int s, bool in_list) -> int8_t {
+            if (s == px) return in_list ? NX_IN_SRC : NX_OUT_SRC;
+            if (s == py) return in_list ? NX_IN_DST : NX_OUT_DST;
+            return NX_NONE;
+        };
         if (slot[x] >= 0 && slot[y] >= 0) {
             lp.kind = CLOSE; lp.a = (int8_t)slot[x]; lp.b = (int8_t)slot[y];
+            lp.nx_a = succ(lp.a, false);
+            lp.nx_b = succ(lp.b, true);
         } else if (slot[x] >= 0) {
             lp.kind = EXT_OUT; lp.a = (int8_t)slot[x]; slot[y] = nb++; lp.nl0 = m->nlabel[y];
+            lp.nx_a = succ(lp.a, false);
         } else if (slot[y] >= 0) {
             lp.kind = EXT_IN; lp.a = (int8_t)slot[y]; slot[x] = nb++; lp.nl0 = m->nlabel[x];
+            lp.nx_a = succ(lp.a, true);
         } else {
             lp.kind = FREE; slot[x] = nb++; slot[y] = nb++; lp.nl0 = m->nlabel[x]; lp.nl1 = m->nlabel[y];
         }
@@ -109,9 +122,9 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
     p.warp_smem = std::max(16, (off_c + 15) & ~15);
     p.warp_smem_fill = std::max(16, (off_f + 15) & ~15);
     p.tune.warps_per_block = 4;
-    p.tune.chunk_roots = 256;
-    p.tune.split_depth = k >= 3 ? 1 : (k == 2 ? 0 : -1);
-    p.tune.split_min = 256;
+    p.tune.chunk_roots = 64;
+    p.tune.split_depth = k >= 3 ? 2 : (k == 2 ? 1 : 0);
+    p.tune.split_min = 512;
     p.shape_hash = plan_shape_hash(m);
     *out = p;
     return TM_OK;
@@ -313,7 +326,7 @@ extern "C" tm_status tm_query_free(tm_query* q) {
 extern "C" tm_status tm_query_set_tuning(tm_query* q, const tm_tuning* t) {
     if (!q || !t) { set_error("null argument"); return TM_E_INVALID; }
     if (t->warps_per_block < 1 || t->warps_per_block > 16 || t->chunk_roots < 32 || (t->chunk_roots % 32) != 0 ||
-        t->split_min < 0 || t->split_depth < -1 || t->split_depth > TM_MAX_EDGES) {
+        t->split_min < 0 || t->split_depth < -1 || t->split_depth > TM_MAX_EDGES - 1) {
         set_error("tuning out of range");
         return TM_E_INVALID;
     }
@@ -579,15 +592,15 @@ extern "C" tm_status tm_autotune(tm_graph* g, tm_query* q, void* stream, tm_tuni
         tm_status s = time_cfg(best, &best_ms);
         // coordinate descent over the four knobs
         const int warps_c[] = {2, 4, 8};
-        const int chunk_c[] = {64, 256, 1024};
-        const int min_c[] = {64, 256, 2048};
+        const int chunk_c[] = {32, 64, 256};
+        const int min_c[] = {128, 512, 4096};
         for (int knob = 0; knob < 4 && s == TM_OK; ++knob) {
             std::vector<tm_tuning> cands;
             for (int i = 0; i < 3; ++i) {
                 tm_tuning t = best;
                 if (knob == 0) t.warps_per_block = warps_c[i];
                 if (knob == 1) t.chunk_roots = chunk_c[i];
-                if (knob == 2) { t.split_depth = i - 1; if (t.split_depth > q->plan.k - 2) continue; }
+                if (knob == 2) { t.split_depth = i; if (t.split_depth > q->plan.k - 1) continue; }
                 if (knob == 3) t.split_min = min_c[i];
                 cands.push_back(t);
             }

@@ -96,12 +96,59 @@ __global__ void offsets_kernel(const unsigned long long* __restrict__ off64, int
 
 __global__ void list_columns_kernel(const uint32_t* __restrict__ eids, int64_t m, const int64_t* __restrict__ t,
                                     const int32_t* __restrict__ other, int64_t* __restrict__ at,
-                                    int32_t* __restrict__ anbr, int32_t* __restrict__ aeid) {
+                                    int32_t* __restrict__ anbr, int32_t* __restrict__ aeid,
+                                    uint32_t* __restrict__ pos_of_edge) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t e = eids[i];
         at[i] = t[e];
         anbr[i] = other[e];
         aeid[i] = (int32_t)e;
+        pos_of_edge[e] = (uint32_t)i;
+    }
+}
+
+// first index in [lo, hi) with t[idx] > x
+__device__ __forceinline__ uint32_t first_later(const int64_t* __restrict__ t, uint32_t lo, uint32_t hi, int64_t x) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (t[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// first index in [beg, hi) with t[idx] > x, searching outward from beg
+__device__ __forceinline__ uint32_t first_later_from(const int64_t* __restrict__ t, uint32_t beg, uint32_t hi,
+                                                     int64_t x) {
+    uint32_t a = beg, b = hi, step = 1;
+    while (true) {
+        uint32_t probe = a + step - 1;
+        if (probe >= hi) { b = hi; break; }
+        if (t[probe] > x) { b = probe; break; }
+        a = probe + 1;
+        step <<= 1;
+    }
+    return first_later(t, a, b, x);
+}
+
+// Successor index: for every edge e = (u, v, t), the first position after t in
+// each of the four lists that touch it: out(u), in(v) (where e itself sits,
+// so the search starts just past e), out(v) and in(u).  A search level whose
+// candidate list belongs to an endpoint of the previous level's edge reads
+// its window start here instead of binary-searching the list.
+__global__ void successor_kernel(int64_t m, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                 const int64_t* __restrict__ t, const uint32_t* __restrict__ off_out,
+                                 const int64_t* __restrict__ at_out, const uint32_t* __restrict__ off_in,
+                                 const int64_t* __restrict__ at_in, const uint32_t* __restrict__ pos_out,
+                                 const uint32_t* __restrict__ pos_in, uint32_t* __restrict__ so_src,
+                                 uint32_t* __restrict__ si_dst, uint32_t* __restrict__ so_dst,
+                                 uint32_t* __restrict__ si_src) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = src[e], v = dst[e];
+        const int64_t te = t[e];
+        so_src[e] = first_later_from(at_out, pos_out[e] + 1, off_out[u + 1], te);
+        si_dst[e] = first_later_from(at_in, pos_in[e] + 1, off_in[v + 1], te);
+        so_dst[e] = first_later(at_out, off_out[v], off_out[v + 1], te);
+        si_src[e] = first_later(at_in, off_in[u], off_in[u + 1], te);
     }
 }
 
@@ -248,9 +295,11 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
     size_t stemp_bytes = scan_temp_bytes((uint64_t)(n + 1));
     void* stemp;
     TRY(tmp.get((char**)&stemp, stemp_bytes));
-    uint32_t *nk_a, *nk_b;
+    uint32_t *nk_a, *nk_b, *pos_edge[2];
     TRY(tmp.get(&nk_a, m));
     TRY(tmp.get(&nk_b, m));
+    TRY(tmp.get(&pos_edge[0], m));
+    TRY(tmp.get(&pos_edge[1], m));
     int nbits = bits_for((unsigned long long)(n > 0 ? n - 1 : 0));
     for (int dir = 0; dir < 2; ++dir) {
         const int32_t* key_node = dir == 0 ? s_o : d_o;
@@ -277,12 +326,24 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
             note_launches(1);
             TM_CUDA(cudaGetLastError());
             TRY(radix_sort_pairs32(nk_a, nk_b, perm_a, perm_b, (uint64_t)m, nbits, rtemp, rtemp_bytes, st));
-            list_columns_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, t_o, other, at, anbr, aeid);
+            list_columns_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, t_o, other, at, anbr, aeid,
+                                                                   pos_edge[dir]);
             note_launches(1);
             TM_CUDA(cudaGetLastError());
         }
         v.off[dir] = off; v.at[dir] = at; v.anbr[dir] = anbr; v.aeid[dir] = aeid;
     }
+    // 5. successor index (window starts for lists that touch the previous edge)
+    uint32_t* nx[4];
+    for (int j = 0; j < 4; ++j) TRY(owned(g, &nx[j], m));
+    if (m > 0) {
+        successor_kernel<<<grid_for(m, sms), 256, 0, st>>>(m, s_o, d_o, t_o, v.off[0], v.at[0], v.off[1], v.at[1],
+                                                           pos_edge[0], pos_edge[1], nx[NX_OUT_SRC], nx[NX_IN_DST],
+                                                           nx[NX_OUT_DST], nx[NX_IN_SRC]);
+        note_launches(1);
+        TM_CUDA(cudaGetLastError());
+    }
+    for (int j = 0; j < 4; ++j) v.nxt[j] = nx[j];
     TM_CUDA(cudaStreamSynchronize(st));
     return TM_OK;
 }

@@ -120,6 +120,7 @@ struct Search {
     Acc acc;
     // enumerate fill
     unsigned long long out_base, out_local;
+    unsigned polls;           // donation checks (warp-uniform)
 
     __device__ Search(const GraphView& g_, const QueryDev* qs_, Ctrl* c, Task* t, uint8_t* r, uint64_t cap, char* wb)
         : g(g_), qs(qs_), ctrl(c), tasks(t), ready(r), task_cap(cap), wbase(wb) {
@@ -129,6 +130,7 @@ struct Search {
         acc.total = 0;
         if (STATS) for (int i = 0; i < W_LEN; ++i) acc.w[i] = 0;
         out_base = out_local = 0;
+        polls = 0;
     }
 
     __device__ uint32_t P(int l) const { return __shfl_sync(FULL, myP, l); }
@@ -166,36 +168,46 @@ struct Search {
 
     // Window for motif edge `lv_i` of a (child) partial match whose slots are
     // parent slots [0, nb) of frame `pf` at index `ps`, plus new nodes n0, n1
-    // at slots nb, nb+1.  Returns len; beg gets bit 31 for in-lists.
-    __device__ uint32_t locate(int lv_i, Frame pf, int ps, int nb, int32_t n0, int32_t n1,
+    // at slots nb, nb+1; prev_e is the edge just bound (time tprev).  The
+    // window's lower end comes from the successor index when the list belongs
+    // to an endpoint of prev_e, else from a binary search; the upper end from
+    // a galloping search.  Returns len; beg gets bit 31 for in-lists.
+    __device__ uint32_t locate(int lv_i, Frame pf, int ps, int nb, int32_t n0, int32_t n1, int32_t prev_e,
                                int64_t tprev, int64_t tend, uint32_t& beg_out) {
         const LevelPlan& lp = q->plan.lv[lv_i];
         auto slot = [&](int s) -> int32_t { return s < nb ? pf.node(s, ps) : (s == nb ? n0 : n1); };
         int64_t lim = min(tend, sat_add(tprev, lp.gap));
         const int64_t* tarr;
-        uint32_t lo, hi, flag = 0;
+        uint32_t b, hi, flag = 0;
         int kind = lp.kind;
         if (kind == FREE) {
-            tarr = g.t; lo = 0; hi = (uint32_t)g.m;
+            tarr = g.t;
+            hi = (uint32_t)g.m;
+            b = gallop_end(tarr, (uint32_t)prev_e + 1u, hi, tprev);
+            if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi);
         } else {
-            int dir;
-            int32_t v;
-            if (kind == EXT_OUT) { dir = 0; v = slot(lp.a); }
-            else if (kind == EXT_IN) { dir = 1; v = slot(lp.a); }
-            else {
+            int dir, nx;
+            uint32_t lo;
+            if (kind == CLOSE) {
+                // the shorter of out(phi(x_i)) and in(phi(y_i))
                 int32_t u = slot(lp.a), w = slot(lp.b);
-                uint32_t du = __ldg(g.off[0] + u + 1) - __ldg(g.off[0] + u);
-                uint32_t dw = __ldg(g.off[1] + w + 1) - __ldg(g.off[1] + w);
-                if (du <= dw) { dir = 0; v = u; } else { dir = 1; v = w; }
+                uint32_t u0 = __ldg(g.off[0] + u), u1 = __ldg(g.off[0] + u + 1);
+                uint32_t w0 = __ldg(g.off[1] + w), w1 = __ldg(g.off[1] + w + 1);
+                if (u1 - u0 <= w1 - w0) { dir = 0; lo = u0; hi = u1; nx = lp.nx_a; }
+                else { dir = 1; lo = w0; hi = w1; nx = lp.nx_b; }
+            } else {
+                dir = kind == EXT_IN ? 1 : 0;
+                int32_t v = slot(lp.a);
+                nx = lp.nx_a;
+                hi = __ldg(g.off[dir] + v + 1);
+                lo = (nx >= 0 && !STATS) ? 0u : __ldg(g.off[dir] + v);
             }
-            lo = __ldg(g.off[dir] + v);
-            hi = __ldg(g.off[dir] + v + 1);
             tarr = g.at[dir];
             flag = dir ? INLIST : 0u;
+            b = nx >= 0 ? __ldg(g.nxt[nx] + prev_e) : upper_bound_t(tarr, lo, hi, tprev);
+            if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi - lo);
         }
-        uint32_t b = upper_bound_t(tarr, lo, hi, tprev);
         uint32_t e = (b < hi) ? gallop_end(tarr, b, hi, lim) : b;
-        if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi - lo);
         beg_out = b | flag;
         return e - b;
     }
@@ -272,7 +284,9 @@ struct Search {
         int64_t ct = 0;
         bool ok = act;
         const int kind = lp.kind;
-        const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0;
+        // the candidate's edge id: written by enumeration, read by edge labels and
+        // by the next level's successor-index lookup
+        const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0 || i < k - 1;
         if (act) {
             uint32_t bw = f.beg(p);
             uint32_t pos = (bw & ~INLIST) + (idx - f.pre(p));
@@ -314,7 +328,7 @@ struct Search {
         int64_t tend = 0;
         if (ok) {
             tend = f.tend(p);
-            clen = locate(i + 1, f, p, nb, n0, n1, ct, tend, cbeg);
+            clen = locate(i + 1, f, p, nb, n0, n1, ceid, ct, tend, cbeg);
         }
         if (STATS) {
             unsigned b = __ballot_sync(FULL, ok);
@@ -354,6 +368,7 @@ struct Search {
         const uint32_t np = P(i), off = Off(i), tot = T(i);
         const tm_tuning& tu = q->plan.tune;
         if (i > tu.split_depth || tot - off <= (uint32_t)tu.split_min) return;
+        if ((++polls & 15u) != 1u) return;      // look at the idle count every 16th step
         int idle = 0;
         if (lane == 0) idle = *(volatile int*)&ctrl->idle;
         idle = __shfl_sync(FULL, idle, 0);
@@ -370,6 +385,10 @@ struct Search {
         }
         const int p0 = lo;
         const int ntask = (int)np - p0;
+        // a task is one parent's window range: donate only when the tasks carry
+        // split_min candidates each on average, else the queue traffic costs
+        // more than the work it moves
+        if ((tot - mid) < (uint32_t)ntask * (uint32_t)max(tu.split_min, 32)) return;
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctrl->q_reserve, (unsigned long long)ntask);
         base = __shfl_sync(FULL, base, 0);
@@ -453,7 +472,7 @@ struct Search {
             int64_t tend = 0;
             if (ok) {
                 tend = sat_add(tt, pl.delta);
-                clen = locate(1, Frame{wbase}, 0, 0, s, d, tt, tend, cbeg);
+                clen = locate(1, Frame{wbase}, 0, 0, s, d, (int32_t)r, tt, tend, cbeg);
             }
             if (STATS) {
                 unsigned b = __ballot_sync(FULL, ok);
@@ -592,15 +611,19 @@ struct Search {
                     atomicSub(&ctrl->busy, 1);
                     atomicAdd(&ctrl->idle, 1);
                     uint64_t t0 = now_ns();
-                    unsigned ns = 32;
+                    unsigned ns = 256;
                     while (true) {
-                        int b = *(volatile int*)&ctrl->busy;
-                        __threadfence();
                         if (!queue_empty()) { atomicAdd(&ctrl->busy, 1); break; }
-                        if (b == 0) { leave = 1; break; }
+                        int b = *(volatile int*)&ctrl->busy;
+                        if (b == 0) {
+                            // no warp holds work: leave unless a donation landed meanwhile
+                            __threadfence();
+                            if (queue_empty()) { leave = 1; break; }
+                            continue;
+                        }
                         if (now_ns() - t0 > WAIT_NS) { leave = 1; break; }
-                        __nanosleep(ns);
-                        if (ns < 1024) ns <<= 1;
+                        __nanosleep(ns);     // back off: waiting warps poll one shared line
+                        if (ns < 8192) ns <<= 1;
                     }
                     atomicSub(&ctrl->idle, 1);
                 }

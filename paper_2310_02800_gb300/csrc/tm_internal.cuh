@@ -43,7 +43,12 @@ struct GraphView {
     const int64_t* at[2];     // list entry time
     const int32_t* anbr[2];   // list entry neighbour (dst for out, src for in)
     const int32_t* aeid[2];   // list entry edge id
+    // successor index, by edge id e = (u, v, t): first position with time > t in
+    // out(u), in(v), out(v), in(u) (absolute positions in the list columns)
+    const uint32_t* nxt[4];
 };
+
+enum SuccKind : int8_t { NX_OUT_SRC = 0, NX_IN_DST = 1, NX_OUT_DST = 2, NX_IN_SRC = 3, NX_NONE = -1 };
 
 struct TuneKey {
     uint64_t shape;     // motif structure hash
@@ -84,7 +89,8 @@ struct LevelPlan {
     int16_t elabel;    // -1 = any
     int16_t nl0;       // label of the (first) new node, -1 = any
     int16_t nl1;       // FREE: label of the second new node (y_i)
-    int16_t pad;
+    int8_t nx_a;       // SuccKind giving the window start of the list used by EXT / CLOSE(out) levels
+    int8_t nx_b;       // SuccKind for the in-list option of a CLOSE level
     int32_t frame_off;       // byte offset of this level's frame in a warp's shared block (count)
     int32_t frame_off_fill;  // same, enumerate-fill layout (frames also carry edge ids)
     int32_t pad2;
