@@ -232,8 +232,8 @@ tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, int nq, void*
  * streams and memory free up (continuous batching). */
 typedef struct {
     uint64_t mem_budget_bytes;   /* device bytes for match buffers + scratch (0 = 4 GiB) */
-    int32_t streams;             /* concurrent batches in flight (0 = 4) */
-    int32_t max_batch;           /* queries per launched batch (0 = 64) */
+    int32_t streams;             /* concurrent batches in flight (0 = 2) */
+    int32_t max_batch;           /* queries per launched batch (0 = 16) */
 } tm_serve_cfg;
 
 typedef struct {

@@ -5,11 +5,11 @@
 // memory (match buffer + per-chunk counts for enumeration) fits the budget,
 // and launches them as ONE multi-query persistent search on the slot's
 // stream: a count launch for every admitted request, then (for enumerate
-// requests) a chunk-offset scan and a multi-query fill launch.  Each slot's
-// grid is sized to its share of the GPU, so batches on different slots run
-// side by side and a request that arrives while others run starts as soon as
-// a slot frees, without waiting for the rest of the GPU.  Completion is
-// detected with CUDA events; results stay on the device until released.
+// requests) a chunk-offset scan and a multi-query fill launch.  Every launch
+// is a full-GPU persistent grid; with two slots, the next batch's blocks take
+// the SMs that the running batch releases during its tail, and a request that
+// arrives while a batch runs is launched as soon as a slot frees.  Completion
+// is detected with CUDA events; results stay on the device until released.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -271,10 +271,10 @@ extern "C" tm_status tm_serve_start(tm_graph* g, const tm_serve_cfg* cfg, tm_ser
     s->g = g;
     s->cfg = cfg ? *cfg : tm_serve_cfg{0, 0, 0};
     if (s->cfg.mem_budget_bytes == 0) s->cfg.mem_budget_bytes = 4ull << 30;
-    if (s->cfg.streams <= 0) s->cfg.streams = 4;
+    if (s->cfg.streams <= 0) s->cfg.streams = 2;
     if (s->cfg.streams > 32) s->cfg.streams = 32;
-    if (s->cfg.max_batch <= 0) s->cfg.max_batch = 64;
-    s->grid_share = std::max(1, g->num_sms / s->cfg.streams);
+    if (s->cfg.max_batch <= 0) s->cfg.max_batch = 16;
+    s->grid_share = g->num_sms;
     s->slots.resize(s->cfg.streams);
     for (Slot& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||

@@ -263,3 +263,22 @@ def test_powerlaw_10m_sampled_roots(tmg):
         for a in (0, m // 3, m - 20_000):
             _, want = og.count(mo, a, a + 20_000, per_root=True)
             assert np.array_equal(prn[a:a + 20_000].astype(np.uint64), want), (mo.name, a)
+
+
+def test_hub_skewed_100m_sampled_roots(tmg):
+    """Full 100M-edge hub-skewed workload (labels, gaps): total = sum of per-root counts, and
+    per-root counts equal the oracle's on sampled root ranges, incl. the busiest hub roots."""
+    g = synth.hub_skewed_100m()
+    og = oracle.Graph.from_synth(g)
+    gg = tmg.Graph.from_synth(g)
+    m = g.n_edges
+    for mo in synth.hub_skewed_queries():
+        q = gg.compile(mo)
+        pr = pr_tensor(m)
+        tot = q.count(per_root=pr)
+        prn = pr.cpu().numpy()
+        assert int(prn.sum()) == tot
+        busiest = int(np.argmax(prn))
+        for a in (0, m // 2, max(0, min(m - 5000, busiest - 2500))):
+            _, want = og.count(mo, a, a + 5000, per_root=True)
+            assert np.array_equal(prn[a:a + 5000].astype(np.uint64), want), (mo.name, a)
