@@ -186,6 +186,13 @@ tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, void* stream,
 tm_status tm_query_profile(tm_query* q, int enable);
 tm_status tm_query_last_ms(const tm_query* q, double* search_ms, double* fill_ms);
 
+/* Test hook for the bounded device waits.  kind 1: the next tm_count /
+ * tm_count_roots / tm_query_work call on q stages a task-queue slot that no
+ * warp ever publishes; the warp that pops it gives up after its ~2 s bounded
+ * wait, the kernel finishes normally and the call returns TM_E_TIMEOUT (the
+ * CUDA context stays usable).  kind 0 clears a pending fault. */
+tm_status tm_query_inject_fault(tm_query* q, int kind);
+
 /* Number of CUDA kernels (and CUDA-graph replays) this library has launched
  * since it was loaded, over all threads. */
 uint64_t tm_kernel_launches(void);

@@ -96,6 +96,7 @@ _SIGS = [
     ("tm_query_profile", ctypes.c_int, [_P, ctypes.c_int]),
     ("tm_query_last_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("tm_kernel_launches", ctypes.c_uint64, []),
+    ("tm_query_inject_fault", ctypes.c_int, [_P, ctypes.c_int]),
     ("tm_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tm_last_error", ctypes.c_char_p, []),
 ]
@@ -302,6 +303,10 @@ class Query:
         a, b = ctypes.c_double(), ctypes.c_double()
         _check(lib().tm_query_last_ms(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def inject_fault(self, kind=1):
+        """Test hook: make the next count call exercise the bounded-wait timeout path."""
+        _check(lib().tm_query_inject_fault(self._h, int(kind)))
 
     def autotune(self, stream=None) -> dict:
         t = Tuning()

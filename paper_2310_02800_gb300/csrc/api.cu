@@ -225,6 +225,7 @@ struct tm_query {
     bool profile = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool fill_timed = false;
+    int inject = 0;      // test hook: fault to stage into the next count launch
 };
 
 namespace tmg {
@@ -260,6 +261,12 @@ static tm_status run_count(tm_graph* g, tm_query* q, uint64_t rb, uint64_t re, c
     Ctrl* c = s.ctrl_stage();
     memset(c, 0, sizeof(Ctrl));
     c->total_chunks = nch;
+    if (q->inject == 1) {
+        // one reserved task slot that no warp will ever publish: a warp that
+        // pops it waits out its bounded wait and reports TM_E_TIMEOUT
+        c->q_reserve = 1;
+        q->inject = 0;
+    }
     QueryDev* qd = s.qdev_stage();
     memset(qd, 0, sizeof(QueryDev));
     qd->plan = q->plan;
@@ -351,6 +358,12 @@ extern "C" tm_status tm_query_last_ms(const tm_query* q, double* search_ms, doub
     if (q->fill_timed) TM_CUDA(cudaEventElapsedTime(&b, q->ev[2], q->ev[3]));
     if (search_ms) *search_ms = a;
     if (fill_ms) *fill_ms = q->fill_timed ? b : 0.0;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_query_inject_fault(tm_query* q, int kind) {
+    if (!q || kind < 0 || kind > 1) { set_error("bad fault kind"); return TM_E_INVALID; }
+    q->inject = kind;
     return TM_OK;
 }
 

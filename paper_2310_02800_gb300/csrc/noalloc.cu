@@ -32,7 +32,7 @@ constexpr uint64_t NOALLOC_TASKS = TM_NOALLOC_TASKS;
 
 // byte layout of the static array
 constexpr size_t OFF_CTRL = 0;
-constexpr size_t OFF_QDEV = 256;
+constexpr size_t OFF_QDEV = 512;
 constexpr size_t OFF_READY = (OFF_QDEV + NOALLOC_MAX_QUERIES * sizeof(QueryDev) + 255) / 256 * 256;
 constexpr size_t OFF_TASKS = (OFF_READY + NOALLOC_TASKS + 255) / 256 * 256;
 constexpr size_t NOALLOC_END = OFF_TASKS + NOALLOC_TASKS * sizeof(Task);

@@ -636,7 +636,7 @@ struct Search {
 };
 
 template <int MODE, bool STATS>
-__global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ GraphView g,
+__global__ void __maxnreg__(56) search_kernel(const __grid_constant__ GraphView g,
                                                      const QueryDev* __restrict__ qs, int nq, int warp_smem,
                                                      Ctrl* ctrl, Task* tasks, uint8_t* ready, uint64_t task_cap) {
     extern __shared__ __align__(16) char smem[];

@@ -143,19 +143,23 @@ struct Task {
 };
 static_assert(sizeof(Task) == 64, "task is one 64-byte record");
 
-// Per-launch control block.
+// Per-launch control block.  The root-chunk cursor is claimed by every warp
+// many times per launch; the queue and idle counters are polled by waiting
+// warps: they sit on separate 128-byte lines so polling never delays claims.
 struct Ctrl {
     unsigned long long total_chunks; // root chunks of all queries of the launch
-    unsigned long long next_chunk;   // root-chunk cursor
+    unsigned long long pad0[15];
+    unsigned long long next_chunk;   // root-chunk cursor (own line)
+    unsigned long long pad1[15];
     unsigned long long q_reserve;    // task slots reserved by donors
     unsigned long long q_head;       // next task slot to pop
     int busy;                        // warps holding work
     int idle;                        // warps waiting for tasks
     unsigned int err;                // 0 or TM_E_TIMEOUT
     unsigned int donated;            // tasks donated (diagnostic)
-    unsigned long long pad[2];
+    unsigned long long pad2[12];
 };
-static_assert(sizeof(Ctrl) == 64, "control block is 64 bytes");
+static_assert(sizeof(Ctrl) == 384, "control block is three 128-byte lines");
 
 struct QueryDev {                    // one query of a launch
     Plan plan;

@@ -282,3 +282,18 @@ def test_hub_skewed_100m_sampled_roots(tmg):
         for a in (0, m // 2, max(0, min(m - 5000, busiest - 2500))):
             _, want = og.count(mo, a, a + 5000, per_root=True)
             assert np.array_equal(prn[a:a + 5000].astype(np.uint64), want), (mo.name, a)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(tmg):
+    """A task slot that nothing publishes (host-staged, no GPU fault): the popping warp's
+    bounded wait runs out, the call returns TM_E_TIMEOUT, and the next call is correct."""
+    g = _powerlaw_small(seed=77, n=2000, m=20_000)
+    og = oracle.Graph.from_synth(g)
+    gg = tmg.Graph.from_synth(g)
+    mo = synth.cycle(3, 3600)
+    q = gg.compile(mo)
+    q.inject_fault(1)
+    with pytest.raises(tmg.TMError) as ei:
+        q.count()
+    assert ei.value.status == tmg.E_TIMEOUT
+    assert q.count() == og.count(mo)
