@@ -83,7 +83,6 @@ struct Frame {
     __device__ int64_t& tend(int s) const { return ((int64_t*)(p + F_TEND))[s]; }
     __device__ uint32_t& beg(int s) const { return ((uint32_t*)(p + F_BEG))[s]; }
     __device__ uint32_t& len(int s) const { return ((uint32_t*)(p + F_LEN))[s]; }
-    __device__ uint32_t& pre(int s) const { return ((uint32_t*)(p + F_PRE))[s]; }
     __device__ uint32_t& root(int s) const { return ((uint32_t*)(p + F_ROOT))[s]; }
     __device__ int32_t& node(int j, int s) const { return ((int32_t*)(p + F_NODE))[j * FCAP + s]; }
     // eids follow the nb node rows
@@ -212,26 +211,44 @@ struct Search {
         return e - b;
     }
 
-    // Exclusive prefix of window lengths over a frame's parents; returns total.
-    __device__ uint32_t begin_frame(int i) {
-        Frame f = frame(i);
-        uint32_t np = P(i);
-        const uint32_t p0 = 2u * lane, p1 = p0 + 1u;
-        uint32_t l0 = p0 < np ? f.len(p0) : 0u;
-        uint32_t l1 = p1 < np ? f.len(p1) : 0u;
-        uint32_t s = l0 + l1, inc = s;
+    // Exclusive prefix of the window lengths of a frame's parents, kept in
+    // registers: lane j holds parents 2j and 2j+1.
+    struct Prefix {
+        uint32_t preA, preB, lenA, lenB, tot;
+    };
+    __device__ Prefix prefix(Frame f, uint32_t np) const {
+        const uint32_t a = 2u * lane, b = a + 1u;
+        Prefix r;
+        r.lenA = a < np ? f.len(a) : 0u;
+        r.lenB = b < np ? f.len(b) : 0u;
+        uint32_t s = r.lenA + r.lenB, inc = s;
         for (int d = 1; d < 32; d <<= 1) {
             uint32_t u = __shfl_up_sync(FULL, inc, d);
             if (lane >= d) inc += u;
         }
-        uint32_t ex = inc - s;
-        if (p0 < np) f.pre(p0) = ex;
-        if (p1 < np) f.pre(p1) = ex + l0;
-        uint32_t tot = __shfl_sync(FULL, inc, 31);
-        __syncwarp();
+        r.preA = inc - s;
+        r.preB = r.preA + r.lenA;
+        r.tot = __shfl_sync(FULL, inc, 31);
+        return r;
+    }
+
+    // The parent whose window holds flattened position x (x < total) and its prefix.
+    __device__ void owner(const Prefix& pr, uint32_t x, int& p, uint32_t& pre_p) const {
+        bool oa = pr.lenA && pr.preA <= x && x - pr.preA < pr.lenA;
+        bool ob = pr.lenB && pr.preB <= x && x - pr.preB < pr.lenB;
+        unsigned ba = __ballot_sync(FULL, oa), bb = __ballot_sync(FULL, ob);
+        int src = ba ? __ffs(ba) - 1 : __ffs(bb) - 1;
+        uint32_t va = __shfl_sync(FULL, pr.preA, src), vb = __shfl_sync(FULL, pr.preB, src);
+        p = 2 * src + (ba ? 0 : 1);
+        pre_p = ba ? va : vb;
+    }
+
+    // Start a frame: its cursor and flattened total.
+    __device__ uint32_t begin_frame(int i) {
+        Prefix pr = prefix(frame(i), P(i));
         setOff(i, 0);
-        setT(i, tot);
-        return tot;
+        setT(i, pr.tot);
+        return pr.tot;
     }
 
     // Emit survivors of the last level (or of the root level when k == 1).
@@ -271,15 +288,20 @@ struct Search {
         const uint32_t np = P(i), off = Off(i), tot = T(i);
         uint32_t idx = off + lane;
         bool act = idx < tot;
-        int p = 0;
-        if (act) {
-            int lo = 0, hi = (int)np;
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (f.pre(mid) <= idx) lo = mid; else hi = mid;
-            }
-            p = lo;
-        }
+        // Lane -> parent without a search: the parent holding `off`, plus the
+        // parents whose windows start inside this 32-wide step (a start mask).
+        Prefix pr = prefix(f, np);
+        int p0;
+        uint32_t pre0;
+        owner(pr, off, p0, pre0);
+        const int a = 2 * lane, b = a + 1;
+        unsigned mk = 0;
+        if (a > p0 && pr.lenA && pr.preA - off < 32u) mk |= 1u << (pr.preA - off);
+        if (b > p0 && pr.lenB && pr.preB - off < 32u) mk |= 1u << (pr.preB - off);
+        const unsigned starts = __reduce_or_sync(FULL, mk);
+        const unsigned le = starts & ((2u << lane) - 1u);
+        const int p = p0 + __popc(le);
+        const uint32_t within = le ? (uint32_t)(lane - (31 - __clz(le))) : (off - pre0 + (uint32_t)lane);
         int32_t n0 = -1, n1 = -1, ceid = -1;
         int64_t ct = 0;
         bool ok = act;
@@ -289,7 +311,7 @@ struct Search {
         const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0 || i < k - 1;
         if (act) {
             uint32_t bw = f.beg(p);
-            uint32_t pos = (bw & ~INLIST) + (idx - f.pre(p));
+            uint32_t pos = (bw & ~INLIST) + within;
             if (kind == FREE) {
                 ct = __ldg(g.t + pos);
                 n0 = __ldg(g.src + pos);
@@ -378,12 +400,10 @@ struct Search {
         mid = (mid + 31u) & ~31u;
         if (mid >= tot || mid <= off) return;
         // parent containing mid
-        int lo = 0, hi = (int)np;
-        while (hi - lo > 1) {
-            int m2 = (lo + hi) >> 1;
-            if (f.pre(m2) <= mid) lo = m2; else hi = m2;
-        }
-        const int p0 = lo;
+        Prefix pr = prefix(f, np);
+        int p0;
+        uint32_t pre0;
+        owner(pr, mid, p0, pre0);
         const int ntask = (int)np - p0;
         // a task is one parent's window range: donate only when the tasks carry
         // split_min candidates each on average, else the queue traffic costs
@@ -401,8 +421,8 @@ struct Search {
         const int nb = q->plan.lv[i].nb;
         for (int j = lane; j < ntask; j += 32) {
             int p = p0 + j;
-            uint32_t pre = f.pre(p), len = f.len(p), bw = f.beg(p);
-            uint32_t skip = (p == p0) ? (mid - pre) : 0u;
+            uint32_t len = f.len(p), bw = f.beg(p);
+            uint32_t skip = (p == p0) ? (mid - pre0) : 0u;
             Task* t = tasks + base + j;
             t->query = (int16_t)qi;
             t->level = (int16_t)i;
@@ -417,7 +437,7 @@ struct Search {
         for (int j = lane; j < ntask; j += 32) *(volatile uint8_t*)&ready[base + j] = 1;
         __syncwarp();
         if (lane == 0) {
-            f.len(p0) = mid - f.pre(p0);
+            f.len(p0) = mid - pre0;
             atomicAdd(&ctrl->donated, (unsigned)ntask);
         }
         __syncwarp();

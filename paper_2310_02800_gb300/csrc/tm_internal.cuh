@@ -111,14 +111,13 @@ struct Plan {
 };
 
 // Frame field offsets (bytes, relative to frame start), FCAP entries each.
-//   tprev i64, tend i64, beg u32 (bit 31: in-list), len u32, pre u32, root u32,
+//   tprev i64, tend i64, beg u32 (bit 31: in-list), len u32, root u32,
 //   node[nb] i32, eid[i] i32 (enumerate only)
 constexpr int F_TPREV = 0;
 constexpr int F_TEND = F_TPREV + 8 * FCAP;
 constexpr int F_BEG = F_TEND + 8 * FCAP;
 constexpr int F_LEN = F_BEG + 4 * FCAP;
-constexpr int F_PRE = F_LEN + 4 * FCAP;
-constexpr int F_ROOT = F_PRE + 4 * FCAP;
+constexpr int F_ROOT = F_LEN + 4 * FCAP;
 constexpr int F_NODE = F_ROOT + 4 * FCAP;
 inline int frame_bytes(int nb, int level, bool with_eids) {
     return F_NODE + 4 * FCAP * (nb + (with_eids ? level : 0));

@@ -45,7 +45,7 @@ def _load():
                                     ctypes.c_void_p, ctypes.c_int)
         lib.synth_uniform.argtypes = [u64, i64, i64, i64, ptr, ptr, ptr, cint]
         lib.synth_powerlaw.argtypes = [u64, i64, i64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, i64,
-                                       cint, ptr, ptr, ptr, ptr, cint]
+                                       cint, cint, ptr, ptr, ptr, ptr, cint]
         lib.synth_labels.argtypes = [u64, u64, i64, cint, ptr, cint]
         lib.synth_draws.argtypes = [u64, u64, i64, ptr]
         lib.synth_draws.restype = None
@@ -99,12 +99,13 @@ def uniform_graph(n: int, m: int, tmax: int, seed: int, sort: bool = True) -> Te
 def powerlaw_graph(n: int, m: int, seed: int, alpha: float = 2.1, span: float = 94_608_000.0,
                    amp: float = 0.8, recip_frac: float = 0.10, burst_frac: float = 0.3,
                    burst_mean: float = 300.0, hub_share: float = 0.0, n_hubs: int = 0,
-                   n_labels: int = 0) -> TemporalGraph:
-    """Bursty power-law temporal graph (input order, unsorted)."""
+                   n_labels: int = 0, pa: bool = True) -> TemporalGraph:
+    """Bursty power-law temporal graph (input order, unsorted).  pa: destinations by
+    preferential attachment (copy model); else drawn from the same popularity as sources."""
     src = np.empty(m, np.int32); dst = np.empty(m, np.int32); t = np.empty(m, np.int64)
     el = np.empty(m, np.uint8) if n_labels > 0 else None
     rc = _load().synth_powerlaw(seed, n, m, alpha, span, amp, recip_frac, burst_frac, burst_mean,
-                                hub_share, n_hubs, n_labels, src.ctypes.data, dst.ctypes.data,
+                                hub_share, n_hubs, n_labels, 1 if pa else 0, src.ctypes.data, dst.ctypes.data,
                                 t.ctypes.data, None if el is None else el.ctypes.data, _nthreads())
     assert rc == 0
     return TemporalGraph(n, src, dst, t, el, None, f"powerlaw_n{n}_m{m}_a{alpha}")
@@ -135,10 +136,11 @@ def powerlaw_10m(seed: int = SEED_BASE + 2, scale: float = 1.0) -> TemporalGraph
 
 
 def hub_skewed_100m(seed: int = SEED_BASE + 3, scale: float = 1.0) -> TemporalGraph:
-    """10M nodes, 100M edges, Zipf 1.8, top 0.01% nodes own 20% of endpoints, 16 edge labels, 30 days."""
+    """10M nodes, 100M edges, Zipf 1.8, top 0.01% nodes own 20% of endpoints, 16 edge labels, 30 days.
+    Both endpoints follow the same popularity, so hubs send as much as they receive."""
     n = max(16, int(10_000_000 * scale)); m = max(16, int(100_000_000 * scale))
     g = powerlaw_graph(n, m, seed, alpha=1.8, span=30 * 86_400.0, recip_frac=0.0, burst_frac=0.0,
-                       hub_share=0.2, n_hubs=max(1, n // 10_000), n_labels=16)
+                       hub_share=0.2, n_hubs=max(1, n // 10_000), n_labels=16, pa=False)
     g.name = f"hubskew_{n}n_{m}e"
     return g
 

@@ -104,16 +104,18 @@ int synth_uniform(uint64_t seed, int64_t n, int64_t m, int64_t tmax,
  * closed-form inverse CDF of the continuous weight density on [1, n+1), then a
  * fixed bijective hash maps rank -> node id so hubs are spread over the id space.
  */
-typedef struct { double beta, a, b; int64_t n; uint64_t perm_mul, perm_add; } zipf_t;
+typedef struct { double beta, a, b; int64_t n, r0; uint64_t perm_mul, perm_add; } zipf_t;
 
 static uint64_t gcd_u64(uint64_t a, uint64_t b) { while (b) { uint64_t r = a % b; a = b; b = r; } return a; }
 
-static void zipf_init(zipf_t* z, int64_t n, double alpha, uint64_t seed) {
+/* ranks r0..n-1 follow the weight density; r0 > 0 leaves ranks below r0 to the hubs */
+static void zipf_init(zipf_t* z, int64_t n, double alpha, uint64_t seed, int64_t r0) {
     z->n = n;
+    z->r0 = r0;
     z->beta = 1.0 / (alpha - 1.0);
     double om = 1.0 - z->beta;
-    z->a = 1.0;                              /* (1)^(1-beta) */
-    z->b = pow((double)n + 1.0, om) - 1.0;   /* (n+1)^(1-beta) - 1 */
+    z->a = pow((double)r0 + 1.0, om);                /* (r0+1)^(1-beta) */
+    z->b = pow((double)n + 1.0, om) - z->a;         /* (n+1)^(1-beta) - (r0+1)^(1-beta) */
     uint64_t mul = (draw(seed, 90, 0) % (uint64_t)n) | 1ULL;
     while (gcd_u64(mul, (uint64_t)n) != 1) mul += 2;
     z->perm_mul = mul % (uint64_t)n ? mul % (uint64_t)n : 1;
@@ -122,9 +124,9 @@ static void zipf_init(zipf_t* z, int64_t n, double alpha, uint64_t seed) {
 
 static inline int64_t zipf_rank(const zipf_t* z, double u) {
     double om = 1.0 - z->beta;
-    double x = pow(z->a + u * z->b, 1.0 / om) - 1.0;    /* in [0, n) */
+    double x = pow(z->a + u * z->b, 1.0 / om) - 1.0;    /* in [r0, n) */
     int64_t r = (int64_t)x;
-    if (r < 0) r = 0;
+    if (r < z->r0) r = z->r0;
     if (r >= z->n) r = z->n - 1;
     return r;
 }
@@ -185,7 +187,7 @@ static int64_t pl_dst_raw(const pl_ctx* c, int64_t e) {
 }
 
 static inline int64_t pl_dst(const pl_ctx* c, int64_t e, int64_t s) {
-    int64_t d = pl_dst_raw(c, e);
+    int64_t d = c->copy_p > 0.0 ? pl_dst_raw(c, e) : pl_endpoint(c, 30, (uint64_t)e);
     if (d == s) {                      /* no self-loops: uniform over the others */
         d = (int64_t)below(c->seed, 40, (uint64_t)e, (uint64_t)(c->n - 1));
         if (d >= s) d += 1;
@@ -244,10 +246,12 @@ static void pl_body(void* p, int64_t lo, int64_t hi) {
  *                 mean burst_mean seconds around burst centres)
  *   hub_share, n_hubs : optional hub skew (share of endpoints on the top ranks)
  *   elabel      : optional (nullable) uint8 labels uniform in [0, n_labels)
+ *   pa          : 1 = destinations by preferential attachment (copy model),
+ *                 0 = destinations drawn like sources (hubs both send and receive)
  */
 int synth_powerlaw(uint64_t seed, int64_t n, int64_t m, double alpha, double span,
                    double amp, double recip_frac, double burst_frac, double burst_mean,
-                   double hub_share, int64_t n_hubs, int n_labels,
+                   double hub_share, int64_t n_hubs, int n_labels, int pa,
                    int32_t* src, int32_t* dst, int64_t* t, uint8_t* elabel, int nthreads) {
     if (n < 2 || m < 1 || alpha <= 1.0 || span < 1.0) return 1;
     pl_ctx c;
@@ -259,13 +263,15 @@ int synth_powerlaw(uint64_t seed, int64_t n, int64_t m, double alpha, double spa
     c.m_recip = m - c.m_base;
     c.burst_frac = burst_frac; c.burst_mean = burst_mean;
     c.n_bursts = burst_frac > 0 ? (int64_t)(c.m_base * burst_frac / 50.0) + 1 : 0;
-    c.copy_p = 1.0 / (alpha - 1.0);
+    /* pa != 0: destinations by preferential attachment (copy model);
+       pa == 0: destinations drawn from the same popularity as sources */
+    c.copy_p = pa ? 1.0 / (alpha - 1.0) : 0.0;
     if (c.copy_p > 0.98) c.copy_p = 0.98;
-    zipf_init(&c.zs, n, alpha, seed);
+    c.hub_share = hub_share; c.n_hubs = n_hubs > 0 ? n_hubs : 1;
+    zipf_init(&c.zs, n, alpha, seed, hub_share > 0.0 ? c.n_hubs : 0);
     uint64_t mul = (draw(seed, 92, 0) % (uint64_t)c.m_base) | 1ULL;
     while (gcd_u64(mul, (uint64_t)c.m_base) != 1) mul += 2;
     c.rperm_mul = mul; c.rperm_add = draw(seed, 93, 0) % (uint64_t)c.m_base;
-    c.hub_share = hub_share; c.n_hubs = n_hubs > 0 ? n_hubs : 1;
     c.with_labels = elabel != NULL; c.n_labels = n_labels > 0 ? n_labels : 1;
     c.src = src; c.dst = dst; c.t = t; c.elabel = elabel;
     parallel_for(m, nthreads, pl_body, &c);
