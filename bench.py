@@ -469,7 +469,8 @@ def serve_1b(args, dev):
     gg = tmg.Graph.from_synth(g, device=dev)
     load_s = time.perf_counter() - t0
     del g
-    res = served_leg(gg, dev, duration_s=2.0, dmax=86_400.0, max_requests=200)
+    # delta capped at one hour: day-long 5- and 6-edge stars reach 1e14+ matches on this graph
+    res = served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=60)
     line = {"metric": "p50/p99 latency and throughput, served vs serial", "workload": gg.n_edges,
             "config": {"workload": f"powerlaw_1b x{args.scale}", "n_edges": gg.n_edges, "n_nodes": gg.n_nodes,
                        "device_bytes": gg.device_bytes, "generate_s": gen_s, "load_s": load_s},
