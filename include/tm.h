@@ -22,7 +22,7 @@
  *   - Edge ids: edges are ranked by (t, input index); edge id = rank.  Every
  *     edge id the library reports refers to this order (tm_graph_edge_perm
  *     maps it back to input positions).
- *   - Limits: n_edges < 2^31 - 1, n_nodes < 2^31 - 1, timestamps >= 0
+ *   - Limits: n_edges < 2^30 - 1, n_nodes < 2^31 - 1, timestamps >= 0
  *     (int64 seconds or any unit), k <= 8 motif edges, <= 8 motif nodes.
  */
 #ifndef TM_H

@@ -6,6 +6,8 @@
 //   4. per direction: degree histogram + exclusive scan -> list offsets;
 //      stable radix sort of (endpoint, edge id) -> lists in time order;
 //      gather (t, neighbour) columns for the lists.
+//   5. out-lists re-ordered by (neighbour, time): closing-edge lookups
+//   6. successor index: per edge, the first later position in its four lists
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,6 +106,23 @@ __global__ void list_columns_kernel(const uint32_t* __restrict__ eids, int64_t m
         anbr[i] = other[e];
         aeid[i] = (int32_t)e;
         pos_of_edge[e] = (uint32_t)i;
+    }
+}
+
+__global__ void keys_by_perm_kernel(const int32_t* __restrict__ node, const uint32_t* __restrict__ perm, int64_t m,
+                                    uint32_t* __restrict__ keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = (uint32_t)node[perm[i]];
+}
+
+__global__ void pair_columns_kernel(const uint32_t* __restrict__ eids, int64_t m, const int64_t* __restrict__ t,
+                                    const int32_t* __restrict__ dst, int32_t* __restrict__ pnbr,
+                                    int64_t* __restrict__ pt, int32_t* __restrict__ peid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = eids[i];
+        pnbr[i] = dst[e];
+        pt[i] = t[e];
+        peid[i] = (int32_t)e;
     }
 }
 
@@ -333,7 +352,30 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
         }
         v.off[dir] = off; v.at[dir] = at; v.anbr[dir] = anbr; v.aeid[dir] = aeid;
     }
-    // 5. successor index (window starts for lists that touch the previous edge)
+    // 5. pair-ordered out-lists: stable sorts of the time-ordered edge ids by
+    //    destination, then by source, give (source, destination, time) order
+    {
+        int32_t *pn, *pe;
+        int64_t* ptm;
+        TRY(owned(g, &pn, m));
+        TRY(owned(g, &ptm, m));
+        TRY(owned(g, &pe, m));
+        if (m > 0) {
+            node_keys_kernel<<<grid_for(m, sms), 256, 0, st>>>(d_o, m, nk_a, perm_a);
+            note_launches(1);
+            TM_CUDA(cudaGetLastError());
+            TRY(radix_sort_pairs32(nk_a, nk_b, perm_a, perm_b, (uint64_t)m, nbits, rtemp, rtemp_bytes, st));
+            keys_by_perm_kernel<<<grid_for(m, sms), 256, 0, st>>>(s_o, perm_a, m, nk_a);
+            note_launches(1);
+            TM_CUDA(cudaGetLastError());
+            TRY(radix_sort_pairs32(nk_a, nk_b, perm_a, perm_b, (uint64_t)m, nbits, rtemp, rtemp_bytes, st));
+            pair_columns_kernel<<<grid_for(m, sms), 256, 0, st>>>(perm_a, m, t_o, d_o, pn, ptm, pe);
+            note_launches(1);
+            TM_CUDA(cudaGetLastError());
+        }
+        v.pnbr = pn; v.pt = ptm; v.peid = pe;
+    }
+    // 6. successor index (window starts for lists that touch the previous edge)
     uint32_t* nx[4];
     for (int j = 0; j < 4; ++j) TRY(owned(g, &nx[j], m));
     if (m > 0) {
@@ -356,7 +398,7 @@ using namespace tmg;
 
 extern "C" tm_status tm_graph_load(const tm_edges* e, int device, void* stream, tm_graph** out) {
     if (!e || !out) { set_error("null argument"); return TM_E_INVALID; }
-    if (e->n_edges < 0 || e->n_nodes < 0 || e->n_edges >= 0x7FFFFFFF || e->n_nodes >= 0x7FFFFFFF) {
+    if (e->n_edges < 0 || e->n_nodes < 0 || e->n_edges >= 0x3FFFFFFF || e->n_nodes >= 0x7FFFFFFF) {
         set_error("n_edges / n_nodes out of range");
         return TM_E_INVALID;
     }

@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "tm_internal.cuh"
 
@@ -37,7 +39,10 @@ namespace tmg {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t INLIST = 0x80000000u;
+constexpr uint32_t INLIST = 0x80000000u;    // window in an in-list
+constexpr uint32_t PAIRLIST = 0x40000000u;  // window in the (neighbour, time)-ordered out-list
+constexpr uint32_t POSMASK = 0x3FFFFFFFu;
+constexpr uint32_t PAIR_MIN_DEG = 48;       // closing lookups on shorter lists scan the time window
 constexpr uint64_t WAIT_NS = 20ull * 1000 * 1000 * 1000;      // idle-wait deadline
 constexpr uint64_t READY_NS = 2ull * 1000 * 1000 * 1000;      // publish-wait deadline
 
@@ -74,6 +79,15 @@ __device__ __forceinline__ uint32_t gallop_end(const int64_t* __restrict__ t, ui
 }
 
 __device__ __forceinline__ uint32_t ceil_log2p1(uint32_t x) { return 32 - __clz(x); }  // ceil(log2(x+1))
+
+// first index in [lo, hi) with a[idx] >= x
+__device__ __forceinline__ uint32_t lower_bound_i32(const int32_t* __restrict__ a, uint32_t lo, uint32_t hi, int32_t x) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 // ------------------------------------------------------------ frame access
 
@@ -192,6 +206,16 @@ struct Search {
                 int32_t u = slot(lp.a), w = slot(lp.b);
                 uint32_t u0 = __ldg(g.off[0] + u), u1 = __ldg(g.off[0] + u + 1);
                 uint32_t w0 = __ldg(g.off[1] + w), w1 = __ldg(g.off[1] + w + 1);
+                if (!STATS && min(u1 - u0, w1 - w0) >= PAIR_MIN_DEG) {
+                    // both lists are long: take the u -> w edges straight from the
+                    // pair-ordered out-list of u (neighbour range, then time window)
+                    uint32_t ps = lower_bound_i32(g.pnbr, u0, u1, w);
+                    uint32_t pe = lower_bound_i32(g.pnbr, ps, u1, w + 1);
+                    uint32_t pb = upper_bound_t(g.pt, ps, pe, tprev);
+                    uint32_t pz = (pb < pe) ? gallop_end(g.pt, pb, pe, lim) : pb;
+                    beg_out = pb | PAIRLIST;
+                    return pz - pb;
+                }
                 if (u1 - u0 <= w1 - w0) { dir = 0; lo = u0; hi = u1; nx = lp.nx_a; }
                 else { dir = 1; lo = w0; hi = w1; nx = lp.nx_b; }
             } else {
@@ -311,8 +335,12 @@ struct Search {
         const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0 || i < k - 1;
         if (act) {
             uint32_t bw = f.beg(p);
-            uint32_t pos = (bw & ~INLIST) + within;
-            if (kind == FREE) {
+            uint32_t pos = (bw & POSMASK) + within;
+            if (bw & PAIRLIST) {
+                // closing edge from the pair-ordered list: structure holds by construction
+                ct = __ldg(g.pt + pos);
+                if (need_eid) ceid = __ldg(g.peid + pos);
+            } else if (kind == FREE) {
                 ct = __ldg(g.t + pos);
                 n0 = __ldg(g.src + pos);
                 n1 = __ldg(g.dst + pos);
@@ -667,19 +695,39 @@ __global__ void __maxnreg__(56) search_kernel(const __grid_constant__ GraphView 
 
 }  // namespace
 
+namespace {
+std::mutex g_cfg_mu;
+std::unordered_map<uint64_t, int> g_blocks_per_sm;   // (device, kernel, warps, smem) -> resident blocks per SM
+
+const void* kernel_of(Mode mode, bool stats) {
+    if (mode == MODE_FILL) return (const void*)search_kernel<MODE_FILL, false>;
+    return stats ? (const void*)search_kernel<MODE_COUNT, true> : (const void*)search_kernel<MODE_COUNT, false>;
+}
+
+// Resident blocks per SM for one launch shape, computed once per shape.
+int blocks_per_sm(const tm_graph* g, const void* fn, int kid, int threads, int smem) {
+    uint64_t key = ((uint64_t)g->device << 56) | ((uint64_t)kid << 48) | ((uint64_t)threads << 32) | (uint64_t)smem;
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    auto it = g_blocks_per_sm.find(key);
+    if (it != g_blocks_per_sm.end()) return it->second;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem);
+    cudaGetLastError();
+    if (blocks < 1) blocks = 1;
+    g_blocks_per_sm[key] = blocks;
+    return blocks;
+}
+}  // namespace
+
 LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int warps_per_block) {
     LaunchCfg c;
     c.warps_per_block = std::max(1, std::min(16, warps_per_block));
     // keep the block's frames within the 227 KB of shared memory a block may use
     while (c.warps_per_block > 1 && max_warp_smem * c.warps_per_block > 232448) c.warps_per_block--;
     c.smem_bytes = max_warp_smem * c.warps_per_block;
-    int blocks = 0;
-    const void* fn = mode == MODE_COUNT ? (const void*)search_kernel<MODE_COUNT, false>
-                                        : (const void*)search_kernel<MODE_FILL, false>;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem_bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, c.warps_per_block * 32, c.smem_bytes);
-    if (blocks < 1) blocks = 1;
-    c.grid = blocks * g->num_sms;
+    int kid = mode == MODE_FILL ? 1 : 0;
+    c.grid = blocks_per_sm(g, kernel_of(mode, false), kid, c.warps_per_block * 32, c.smem_bytes) * g->num_sms;
     return c;
 }
 
@@ -690,8 +738,7 @@ tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, 
     dim3 block(c.warps_per_block * 32);
     if (mode == MODE_COUNT) {
         if (stats) {
-            cudaFuncSetAttribute((const void*)search_kernel<MODE_COUNT, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem_bytes);
+            blocks_per_sm(g, kernel_of(MODE_COUNT, true), 2, c.warps_per_block * 32, c.smem_bytes);
             search_kernel<MODE_COUNT, true><<<grid, block, c.smem_bytes, st>>>(
                 g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
             note_launches(1);

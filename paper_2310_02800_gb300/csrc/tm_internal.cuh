@@ -46,6 +46,11 @@ struct GraphView {
     // successor index, by edge id e = (u, v, t): first position with time > t in
     // out(u), in(v), out(v), in(u) (absolute positions in the list columns)
     const uint32_t* nxt[4];
+    // out-lists again, ordered by (neighbour, time) within each node (offsets off[0]):
+    // the edges u -> v form one contiguous, time-ordered range
+    const int32_t* pnbr;
+    const int64_t* pt;
+    const int32_t* peid;
 };
 
 enum SuccKind : int8_t { NX_OUT_SRC = 0, NX_IN_DST = 1, NX_OUT_DST = 2, NX_IN_SRC = 3, NX_NONE = -1 };
