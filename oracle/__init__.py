@@ -22,6 +22,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 MAX_EDGES = 8
 MAX_NODES = 8
+MAX_ANTI = 4
 INT64_MAX = np.iinfo(np.int64).max
 
 
@@ -40,7 +41,10 @@ class Motif(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
                 ("esrc", ctypes.c_uint8 * MAX_EDGES), ("edst", ctypes.c_uint8 * MAX_EDGES),
                 ("delta", ctypes.c_int64), ("gap", ctypes.c_int64 * (MAX_EDGES - 1)),
-                ("elabel", ctypes.c_int16 * MAX_EDGES), ("nlabel", ctypes.c_int16 * MAX_NODES)]
+                ("elabel", ctypes.c_int16 * MAX_EDGES), ("nlabel", ctypes.c_int16 * MAX_NODES),
+                ("n_anti", ctypes.c_int32), ("anti_src", ctypes.c_uint8 * MAX_ANTI),
+                ("anti_dst", ctypes.c_uint8 * MAX_ANTI), ("anti_edge", ctypes.c_uint8 * MAX_ANTI),
+                ("anti_delta", ctypes.c_int64 * MAX_ANTI)]
 
 
 class Work(ctypes.Structure):
@@ -75,8 +79,9 @@ def _load():
     return _lib
 
 
-def make_motif(edges, delta, gaps=None, elabel=None, nlabel=None, n_nodes=None) -> Motif:
-    """Oracle motif struct from plain lists (gaps: k-1 values, None/INT64_MAX = none)."""
+def make_motif(edges, delta, gaps=None, elabel=None, nlabel=None, n_nodes=None, anti=None) -> Motif:
+    """Oracle motif struct from plain lists (gaps: k-1 values, None/INT64_MAX = none;
+    anti: list of (src node, dst node, attached edge index, delta))."""
     k = len(edges)
     q = Motif()
     q.k = k
@@ -91,12 +96,16 @@ def make_motif(edges, delta, gaps=None, elabel=None, nlabel=None, n_nodes=None) 
         q.elabel[i] = -1 if elabel is None or i >= len(elabel) else int(elabel[i])
     for i in range(MAX_NODES):
         q.nlabel[i] = -1 if nlabel is None or i >= len(nlabel) else int(nlabel[i])
+    anti = anti or []
+    q.n_anti = len(anti)
+    for a, (x, y, e, d) in enumerate(anti):
+        q.anti_src[a] = x; q.anti_dst[a] = y; q.anti_edge[a] = e; q.anti_delta[a] = int(d)
     return q
 
 
 def motif_from(m) -> Motif:
     """Oracle motif struct from a synth.Motif-like object."""
-    return make_motif(m.edges, m.delta, m.gaps, m.elabel, m.nlabel)
+    return make_motif(m.edges, m.delta, m.gaps, m.elabel, m.nlabel, anti=getattr(m, "anti", None))
 
 
 class Graph:

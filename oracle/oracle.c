@@ -16,6 +16,9 @@
  *     4. an injective map phi: motif nodes -> graph nodes with
  *        src(e_i) = phi(x_i), dst(e_i) = phi(y_i)     (isomorphism semantics)
  *     5. label equalities on edges / nodes where given (Section 5.4.1)
+ *     6. for every temporal anti-edge (x', y', delta') attached to motif edge i:
+ *        no graph edge other than e_i goes from phi(x') to phi(y') at a time in
+ *        the closed interval [t(e_i), t(e_i) + delta']       (Section 2.1)
  *
  * How: the chronological depth-first search of Algorithm 1 (Section 2.2,
  * Mackey et al.), with its execution context MapMG / MapGM / eCount / eStack,
@@ -34,6 +37,8 @@
  *     deg_out(phi(x)) <= deg_in(phi(y)), else N_in(phi(y)) (the listing leaves
  *     the choice open; the smaller list is the cheap one);
  *   - the fine-grained limit for edge i is t(e_{i-1}) + gap_{i-1}, saturating.
+ * Algorithm 1 has no anti-edges; here they are tested on each complete match,
+ * straight from their definition, before the match is counted.
  * Iterating every candidate list in ascending edge id makes the enumeration
  * come out in lexicographic order of (e_0, ..., e_{k-1}).
  */
@@ -192,8 +197,26 @@ static int64_t upper_by_time(const or_graph* g, const int64_t* list, int64_t lo,
     return a;
 }
 
+/* condition 6: is some edge other than e_i from phi(x') to phi(y') inside
+ * [t(e_i), t(e_i) + delta'] for an anti-edge (x', y', delta') attached to e_i? */
+static int anti_edge_present(const ctx_t* c, int a) {
+    const or_graph* g = c->g;
+    const or_motif* q = c->q;
+    int64_t ei = c->estack[q->anti_edge[a]];
+    int64_t u = c->map_mg[q->anti_src[a]], v = c->map_mg[q->anti_dst[a]];
+    int64_t t0 = g->t[ei], t1 = sat_add(t0, q->anti_delta[a]);
+    for (int64_t p = g->out_off[u]; p < g->out_off[u + 1]; ++p) {
+        int64_t e = g->out_eid[p];
+        if (e == ei || g->dst[e] != v) continue;
+        if (g->t[e] >= t0 && g->t[e] <= t1) return 1;
+    }
+    return 0;
+}
+
 static void emit(ctx_t* c) {
     int k = c->q->k;
+    for (int a = 0; a < c->q->n_anti; ++a)
+        if (anti_edge_present(c, a)) return;
     if (c->out && c->written < c->cap) {
         for (int i = 0; i < k; ++i) c->out[c->written * (uint64_t)k + (uint64_t)i] = (int32_t)c->estack[i];
         c->written++;
@@ -246,6 +269,17 @@ static int check_motif(const or_motif* q) {
         if (q->esrc[i] == q->edst[i]) return 0;
     }
     for (int i = 0; i + 1 < q->k; ++i) if (q->gap[i] < 0) return 0;
+    if (q->n_anti < 0 || q->n_anti > OR_MAX_ANTI) return 0;
+    for (int a = 0; a < q->n_anti; ++a) {
+        if (q->anti_src[a] >= q->n_nodes || q->anti_dst[a] >= q->n_nodes) return 0;
+        int used_x = 0, used_y = 0;   /* both ends must be nodes some motif edge binds */
+        for (int i = 0; i < q->k; ++i) {
+            used_x |= q->esrc[i] == q->anti_src[a] || q->edst[i] == q->anti_src[a];
+            used_y |= q->esrc[i] == q->anti_dst[a] || q->edst[i] == q->anti_dst[a];
+        }
+        if (!used_x || !used_y) return 0;
+        if (q->anti_src[a] == q->anti_dst[a] || q->anti_edge[a] >= q->k || q->anti_delta[a] < 0) return 0;
+    }
     return 1;
 }
 

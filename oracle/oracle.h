@@ -9,6 +9,7 @@
 
 #define OR_MAX_EDGES 8
 #define OR_MAX_NODES 8
+#define OR_MAX_ANTI 4
 
 typedef struct {
     int32_t k;                     /* motif edges, in temporal order */
@@ -19,6 +20,11 @@ typedef struct {
     int64_t gap[OR_MAX_EDGES - 1]; /* t_{i+1} - t_i bound, INT64_MAX = none */
     int16_t elabel[OR_MAX_EDGES];  /* -1 = any */
     int16_t nlabel[OR_MAX_NODES];  /* -1 = any */
+    int32_t n_anti;                /* temporal anti-edges (Section 2.1) */
+    uint8_t anti_src[OR_MAX_ANTI]; /* motif node of the absent edge's source */
+    uint8_t anti_dst[OR_MAX_ANTI];
+    uint8_t anti_edge[OR_MAX_ANTI];/* motif edge it is attached to */
+    int64_t anti_delta[OR_MAX_ANTI];
 } or_motif;
 
 typedef struct {

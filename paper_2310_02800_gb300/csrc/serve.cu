@@ -256,7 +256,14 @@ void scheduler(tm_server* s) {
                 continue;
             }
         }
-        s->cv_work.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+        if (any_busy) {
+            // batches in flight: poll their events at microsecond granularity
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else {
+            s->cv_work.wait_for(lk, std::chrono::microseconds(2000));
+        }
     }
 }
 
@@ -286,6 +293,14 @@ extern "C" tm_status tm_serve_start(tm_graph* g, const tm_serve_cfg* cfg, tm_ser
         }
     }
     cudaStreamCreateWithFlags(&s->free_st, cudaStreamNonBlocking);
+    // keep freed match buffers in the device's stream-ordered pool instead of
+    // returning them to the driver at every synchronisation
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) {
+        uint64_t keep = s->cfg.mem_budget_bytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
     s->th = std::thread(scheduler, s);
     *out = s;
     return TM_OK;

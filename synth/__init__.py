@@ -167,6 +167,7 @@ class Motif:
     elabel: list = field(default_factory=list)    # k entries, -1 = any
     nlabel: list = field(default_factory=list)    # n_nodes entries, -1 = any
     name: str = ""
+    anti: list = field(default_factory=list)      # (src node, dst node, attached edge, delta) per anti-edge
 
     def __post_init__(self):
         k = len(self.edges)

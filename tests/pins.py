@@ -20,8 +20,10 @@ def edge_order(t):
 
 
 def brute_force(src, dst, t, edges, delta, gaps=None, elabel=None, nlabel=None,
-                edge_labels=None, node_labels=None):
-    """Every k-subset of edges in id order, tested against conditions 1-5 of the definition.
+                edge_labels=None, node_labels=None, anti=None):
+    """Every k-subset of edges in id order, tested against conditions 1-6 of the definition
+    (6: for each anti-edge (x, y, i, d), no edge other than e_i from phi(x) to phi(y) with
+    time in [t(e_i), t(e_i) + d]).
 
     Returns the sorted list of matches (tuples of edge ids) -- exhaustive, so
     only for tiny graphs (C(m, k) subsets).
@@ -57,6 +59,10 @@ def brute_force(src, dst, t, edges, delta, gaps=None, elabel=None, nlabel=None,
             continue
         if nlabel is not None and any(nlabel[mn] >= 0 and (node_labels is None or node_labels[gn] != nlabel[mn])
                                       for mn, gn in phi.items()):
+            continue
+        if anti and any(any(e2 != combo[ai] and S[e2] == phi[ax] and D[e2] == phi[ay]
+                            and T[combo[ai]] <= T[e2] <= T[combo[ai]] + ad for e2 in range(m))
+                        for ax, ay, ai, ad in anti):
             continue
         out.append(combo)
     return out

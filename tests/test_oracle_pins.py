@@ -151,8 +151,12 @@ def test_walkthrough_golden():
     for case in spec["cases"]:
         e = np.array(case["edges"], np.int64)
         og = oracle.Graph(int(e[:, :2].max()) + 1, e[:, 0].astype(np.int32), e[:, 1].astype(np.int32), e[:, 2])
-        q = oracle.make_motif([tuple(x) for x in case["motif"]], case["delta"], case["gaps"])
+        anti = [tuple(a) for a in case.get("anti", [])]
+        q = oracle.make_motif([tuple(x) for x in case["motif"]], case["delta"], case["gaps"], anti=anti)
         assert og.count(q) == case["expected_count"], case["reason"]
+        want = pins.brute_force(e[:, 0], e[:, 1], e[:, 2], [tuple(x) for x in case["motif"]], case["delta"],
+                                case["gaps"], anti=anti)
+        assert len(want) == case["expected_count"], case["reason"]
 
 
 def _pl_small(seed=5, m=30000):
@@ -261,3 +265,43 @@ def test_degenerate_inputs():
     src = np.array([a for a, _ in e8], np.int32); dst = np.array([b for _, b in e8], np.int32)
     og = oracle.Graph(8, src, dst, np.arange(8, dtype=np.int64) * 10)
     assert og.count(synth.Motif(e8, 70)) == 1 and og.count(synth.Motif(e8, 69)) == 0
+
+
+ANTI_CASES = [
+    ([(0, 1), (1, 2), (2, 0)], [(0, 2, 0, 5)]),               # no a->c shortly after the first edge
+    ([(0, 1), (1, 2), (2, 0)], [(1, 0, 1, 8), (2, 1, 2, 3)]),  # two anti-edges on later edges
+    ([(0, 1), (1, 0)], [(0, 1, 0, 6)]),                         # anti-edge on the attached edge's own pair
+    ([(0, 1), (0, 2), (0, 3)], [(1, 2, 2, 10)]),                # between two leaves, on the last edge
+    ([(0, 1), (1, 2)], [(2, 0, 0, 0)]),                         # zero-length window (ties only)
+]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_anti_edges_brute_force(seed):
+    """Temporal anti-edges (Section 2.1): the oracle equals exhaustive search on tiny multigraphs."""
+    rng = np.random.default_rng(500 + seed)
+    n_nodes = int(rng.integers(3, 6))
+    m = int(rng.integers(10, 17))
+    src, dst, t, _, _ = rand_graph(rng, n_nodes, m, tmax=int(rng.integers(5, 25)))
+    og = oracle.Graph(n_nodes, src, dst, t)
+    for edges, anti in ANTI_CASES:
+        for delta in (4, 30):
+            want = pins.brute_force(src, dst, t, edges, delta, anti=anti)
+            q = oracle.make_motif(edges, delta, anti=anti)
+            rows, tot = og.enumerate(q)
+            assert [tuple(int(x) for x in r) for r in rows] == want, (edges, anti, delta)
+            assert og.count(q) == len(want)
+            assert og.count(q) <= og.count(oracle.make_motif(edges, delta))
+
+
+def test_anti_edge_monotone_and_vacuous():
+    g = _pl_small(seed=17, m=20000)
+    og = oracle.Graph.from_synth(g)
+    edges = [(0, 1), (1, 2), (2, 0)]
+    base = og.count(oracle.make_motif(edges, 3600))
+    counts = [og.count(oracle.make_motif(edges, 3600, anti=[(0, 2, 0, d)])) for d in (0, 60, 600, 3600)]
+    assert counts == sorted(counts, reverse=True) and counts[0] <= base
+    # an anti-edge between the endpoints of its own edge never counts that edge itself
+    q = oracle.make_motif([(0, 1), (1, 2)], 3600, anti=[(0, 1, 0, 0)])
+    p = oracle.make_motif([(0, 1), (1, 2)], 3600)
+    assert og.count(q) <= og.count(p)
