@@ -46,6 +46,7 @@ typedef enum {
 
 #define TM_MAX_EDGES 8
 #define TM_MAX_NODES 8
+#define TM_MAX_ANTI 4
 
 /* Input edge list (paper Section 2.2: a chronologically ordered temporal edge
  * list; here any order is accepted and the library sorts it).
@@ -74,6 +75,11 @@ typedef struct {
  *   gap[i]     : t(e_{i+1}) - t(e_i) <= gap[i]; INT64_MAX = unconstrained
  *   elabel[i]  : required label of edge i, -1 = any (needs graph elabel)
  *   nlabel[j]  : required label of motif node j, -1 = any (needs graph nlabel)
+ *   n_anti     : temporal anti-edges, 0..4 (Section 2.1, Section 5.4.3).
+ *                Anti-edge a forbids any graph edge other than e_i, with
+ *                i = anti_edge[a], from phi(anti_src[a]) to phi(anti_dst[a])
+ *                at a time in the closed window [t(e_i), t(e_i) + anti_delta[a]].
+ *                Both nodes must appear in some motif edge; anti_delta >= 0.
  * Edge times within a match are strictly increasing; graph self-loops never
  * match (motif edges join distinct nodes). */
 typedef struct {
@@ -85,6 +91,11 @@ typedef struct {
     int64_t gap[TM_MAX_EDGES - 1];
     int16_t elabel[TM_MAX_EDGES];
     int16_t nlabel[TM_MAX_NODES];
+    int32_t n_anti;
+    uint8_t anti_src[TM_MAX_ANTI];
+    uint8_t anti_dst[TM_MAX_ANTI];
+    uint8_t anti_edge[TM_MAX_ANTI];
+    int64_t anti_delta[TM_MAX_ANTI];
 } tm_motif;
 
 /* Execution knobs for one query shape (see tm_autotune).
@@ -94,7 +105,8 @@ typedef struct {
  *   split_depth     : deepest search level whose remaining candidates may be
  *                     donated to idle warps: level i holds the candidate windows
  *                     of motif edge i (1 = the root edges' windows, up to k-1);
- *                     0 or -1 disables donation
+ *                     0 or -1 disables donation (always off for motifs with
+ *                     anti-edges)
  *   split_min       : a donation moves, on average, at least this many
  *                     candidates per donated task */
 typedef struct {

@@ -18,6 +18,7 @@ _SO = os.path.join(_HERE, "libtmgb300.so")
 
 MAX_EDGES = 8
 MAX_NODES = 8
+MAX_ANTI = 4
 INT64_MAX = np.iinfo(np.int64).max
 
 OK, E_INVALID, E_OOM, E_TRUNCATED, E_TIMEOUT, E_CUDA, E_BUSY, E_ADMISSION = range(8)
@@ -39,7 +40,10 @@ class _Motif(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
                 ("esrc", ctypes.c_uint8 * MAX_EDGES), ("edst", ctypes.c_uint8 * MAX_EDGES),
                 ("delta", ctypes.c_int64), ("gap", ctypes.c_int64 * (MAX_EDGES - 1)),
-                ("elabel", ctypes.c_int16 * MAX_EDGES), ("nlabel", ctypes.c_int16 * MAX_NODES)]
+                ("elabel", ctypes.c_int16 * MAX_EDGES), ("nlabel", ctypes.c_int16 * MAX_NODES),
+                ("n_anti", ctypes.c_int32), ("anti_src", ctypes.c_uint8 * MAX_ANTI),
+                ("anti_dst", ctypes.c_uint8 * MAX_ANTI), ("anti_edge", ctypes.c_uint8 * MAX_ANTI),
+                ("anti_delta", ctypes.c_int64 * MAX_ANTI)]
 
 
 class Tuning(ctypes.Structure):
@@ -141,7 +145,8 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_motif(edges, delta, gaps=None, elabel=None, nlabel=None, n_nodes=None) -> _Motif:
+def make_motif(edges, delta, gaps=None, elabel=None, nlabel=None, n_nodes=None, anti=None) -> _Motif:
+    """anti: list of (src node, dst node, attached edge index, delta) temporal anti-edges."""
     m = _Motif()
     m.k = len(edges)
     m.n_nodes = n_nodes if n_nodes is not None else 1 + max(max(e) for e in edges)
@@ -155,6 +160,10 @@ def make_motif(edges, delta, gaps=None, elabel=None, nlabel=None, n_nodes=None) 
         m.elabel[i] = -1 if elabel is None or i >= len(elabel) else int(elabel[i])
     for j in range(MAX_NODES):
         m.nlabel[j] = -1 if nlabel is None or j >= len(nlabel) else int(nlabel[j])
+    anti = anti or []
+    m.n_anti = len(anti)
+    for a, (x, y, e, d) in enumerate(anti):
+        m.anti_src[a] = x; m.anti_dst[a] = y; m.anti_edge[a] = e; m.anti_delta[a] = int(d)
     return m
 
 
@@ -163,7 +172,7 @@ def motif_of(obj) -> _Motif:
     if isinstance(obj, _Motif):
         return obj
     return make_motif(obj.edges, obj.delta, getattr(obj, "gaps", None), getattr(obj, "elabel", None),
-                      getattr(obj, "nlabel", None))
+                      getattr(obj, "nlabel", None), anti=getattr(obj, "anti", None))
 
 
 def _ptr(x):

@@ -42,6 +42,12 @@ uint64_t plan_shape_hash(const tm_motif* m) {
         if (i + 1 < m->k) mix((uint64_t)(m->gap[i] != INT64_MAX));
     }
     for (int j = 0; j < m->n_nodes; ++j) mix((uint64_t)(m->nlabel[j] >= 0));
+    mix((uint64_t)m->n_anti);
+    for (int a = 0; a < m->n_anti; ++a) {
+        mix(m->anti_src[a]);
+        mix(m->anti_dst[a]);
+        mix(m->anti_edge[a]);
+    }
     return h;
 }
 
@@ -65,6 +71,15 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
         if (m->elabel[i] >= 0 && g && !g->v.elabel && g->v.m > 0) { set_error("edge label constraint on a graph without edge labels"); return TM_E_INVALID; }
         if (i + 1 < k && m->gap[i] < 0) { set_error("gap must be >= 0"); return TM_E_INVALID; }
     }
+    if (m->n_anti < 0 || m->n_anti > TM_MAX_ANTI) { set_error("n_anti must be in [0, 4]"); return TM_E_INVALID; }
+    for (int a = 0; a < m->n_anti; ++a) {
+        if (m->anti_src[a] >= nn || m->anti_dst[a] >= nn || !used[m->anti_src[a]] || !used[m->anti_dst[a]] ||
+            m->anti_src[a] == m->anti_dst[a]) {
+            set_error("anti-edge endpoints must be two distinct nodes of the motif's edges");
+            return TM_E_INVALID;
+        }
+        if (m->anti_edge[a] >= k || m->anti_delta[a] < 0) { set_error("anti-edge attached edge or delta out of range"); return TM_E_INVALID; }
+    }
     for (int j = 0; j < nn; ++j) {
         if (!used[j]) { set_error("motif node not used by any edge"); return TM_E_INVALID; }
         if (m->nlabel[j] < -1 || m->nlabel[j] > 255) { set_error("node label out of range"); return TM_E_INVALID; }
@@ -78,10 +93,24 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
     p.elabel0 = m->elabel[0];
     p.nl_x0 = m->nlabel[m->esrc[0]];
     p.nl_y0 = m->nlabel[m->edst[0]];
-    int slot[TM_MAX_NODES];
-    for (int j = 0; j < TM_MAX_NODES; ++j) slot[j] = -1;
+    int slot[TM_MAX_NODES], bound_at[TM_MAX_NODES];
+    for (int j = 0; j < TM_MAX_NODES; ++j) slot[j] = bound_at[j] = -1;
     slot[m->esrc[0]] = 0;
     slot[m->edst[0]] = 1;
+    bound_at[m->esrc[0]] = bound_at[m->edst[0]] = 0;
+    for (int i = 1; i < k; ++i)
+        for (int nd : {(int)m->esrc[i], (int)m->edst[i]})
+            if (bound_at[nd] < 0) bound_at[nd] = i;
+    // anti-edges: checked at the first level where both nodes and the attached edge are bound
+    p.n_anti = m->n_anti;
+    int anti_level[TM_MAX_ANTI];
+    for (int a = 0; a < m->n_anti; ++a) {
+        anti_level[a] = std::max((int)m->anti_edge[a], std::max(bound_at[m->anti_src[a]], bound_at[m->anti_dst[a]]));
+        p.anti[a].edge = (int8_t)m->anti_edge[a];
+        p.anti[a].delta = m->anti_delta[a];
+        p.anti[a].same_pair = m->esrc[m->anti_edge[a]] == m->anti_src[a] && m->edst[m->anti_edge[a]] == m->anti_dst[a];
+        if (anti_level[a] == 0) p.anti_mask0 |= (uint8_t)(1u << a);
+    }
     int nb = 2;
     int off_c = 0, off_f = 0;
     for (int i = 1; i < k; ++i) {
@@ -114,10 +143,18 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
         } else {
             lp.kind = FREE; slot[x] = nb++; slot[y] = nb++; lp.nl0 = m->nlabel[x]; lp.nl1 = m->nlabel[y];
         }
+        for (int a = 0; a < m->n_anti; ++a)
+            if (anti_level[a] == i) lp.anti_mask |= (uint8_t)(1u << a);
         lp.frame_off = off_c;
         lp.frame_off_fill = off_f;
-        off_c += frame_bytes(lp.nb, i, false);
-        off_f += frame_bytes(lp.nb, i, true);
+        lp.anti_row_off = frame_bytes(lp.nb, i, false);
+        lp.anti_row_off_fill = frame_bytes(lp.nb, i, true);
+        off_c += frame_bytes(lp.nb, i, false, m->n_anti);
+        off_f += frame_bytes(lp.nb, i, true, m->n_anti);
+    }
+    for (int a = 0; a < m->n_anti; ++a) {
+        p.anti[a].xs = (int8_t)slot[m->anti_src[a]];
+        p.anti[a].ys = (int8_t)slot[m->anti_dst[a]];
     }
     p.warp_smem = std::max(16, (off_c + 15) & ~15);
     p.warp_smem_fill = std::max(16, (off_f + 15) & ~15);
@@ -125,6 +162,7 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
     p.tune.chunk_roots = 64;
     p.tune.split_depth = k >= 3 ? 2 : (k == 2 ? 1 : 0);
     p.tune.split_min = 512;
+    if (m->n_anti > 0) p.tune.split_depth = 0;   // donated tasks carry no anti-edge times
     p.shape_hash = plan_shape_hash(m);
     *out = p;
     return TM_OK;
@@ -338,6 +376,7 @@ extern "C" tm_status tm_query_set_tuning(tm_query* q, const tm_tuning* t) {
         return TM_E_INVALID;
     }
     q->plan.tune = *t;
+    if (q->plan.n_anti > 0) q->plan.tune.split_depth = 0;   // donated tasks carry no anti-edge times
     q->explicit_tuning = true;
     return TM_OK;
 }

@@ -89,6 +89,17 @@ __device__ __forceinline__ uint32_t lower_bound_i32(const int32_t* __restrict__ 
     return lo;
 }
 
+// Edges u -> v with time in [t0, t1], counted from u's pair-ordered out-list.
+__device__ __forceinline__ uint32_t pair_count(const GraphView& g, int32_t u, int32_t v, int64_t t0, int64_t t1) {
+    uint32_t u0 = __ldg(g.off[0] + u), u1 = __ldg(g.off[0] + u + 1);
+    uint32_t ps = lower_bound_i32(g.pnbr, u0, u1, v);
+    uint32_t pe = lower_bound_i32(g.pnbr, ps, u1, v + 1);
+    if (ps == pe) return 0u;
+    uint32_t a = upper_bound_t(g.pt, ps, pe, t0 - 1);   // first time >= t0 (t0 >= 0)
+    uint32_t b = upper_bound_t(g.pt, a, pe, t1);
+    return b - a;
+}
+
 // ------------------------------------------------------------ frame access
 
 struct Frame {
@@ -101,6 +112,8 @@ struct Frame {
     __device__ int32_t& node(int j, int s) const { return ((int32_t*)(p + F_NODE))[j * FCAP + s]; }
     // eids follow the nb node rows
     __device__ int32_t& eid(int nb, int j, int s) const { return ((int32_t*)(p + F_NODE))[(nb + j) * FCAP + s]; }
+    // anti-edge attached-edge times, at byte offset `row_off` of the frame
+    __device__ int64_t& anti_t(int row_off, int a, int s) const { return ((int64_t*)(p + row_off))[a * FCAP + s]; }
 };
 
 // ------------------------------------------------------------ per-warp state
@@ -155,6 +168,28 @@ struct Search {
 
     __device__ Frame frame(int i) const {
         return Frame{wbase + (MODE == MODE_FILL ? q->plan.lv[i].frame_off_fill : q->plan.lv[i].frame_off)};
+    }
+
+    __device__ int anti_off(int i) const {
+        return MODE == MODE_FILL ? q->plan.lv[i].anti_row_off_fill : q->plan.lv[i].anti_row_off;
+    }
+
+    // Anti-edges in `mask` (Section 2.1): true when none of them has an edge in
+    // its window.  Slots of the candidate's partial match are the parent's
+    // slots [0, nb) plus n0, n1; times: edge `lvl` is the candidate (ct), edge
+    // lvl-1 is the parent's tprev, older attached edges come from anti rows.
+    __device__ bool anti_clear(unsigned mask, int lvl, Frame pf, int ps, int nb, int32_t n0, int32_t n1, int64_t ct,
+                               int64_t tprev, int prow) const {
+        const Plan& pl = q->plan;
+        auto slot = [&](int s) -> int32_t { return s < nb ? pf.node(s, ps) : (s == nb ? n0 : n1); };
+        for (int a = 0; a < pl.n_anti; ++a) {
+            if (!(mask & (1u << a))) continue;
+            const AntiPlan& ap = pl.anti[a];
+            int64_t ti = ap.edge == lvl ? ct : (ap.edge == lvl - 1 ? tprev : pf.anti_t(prow, a, ps));
+            uint32_t c = pair_count(g, slot(ap.xs), slot(ap.ys), ti, sat_add(ti, ap.delta));
+            if (c > (uint32_t)ap.same_pair) return false;
+        }
+        return true;
     }
 
     __device__ void flush() {
@@ -366,6 +401,8 @@ struct Search {
                 }
             }
             if (lp.elabel >= 0) ok &= g.elabel[ceid] == (uint8_t)lp.elabel;
+            if (ok && lp.anti_mask)
+                ok = anti_clear(lp.anti_mask, i, f, p, nb, n0, n1, ct, f.tprev(p), anti_off(i));
         }
         uint32_t root = act ? f.root(p) : 0u;
         if (i == k - 1) {
@@ -408,6 +445,12 @@ struct Search {
                 for (int j = 0; j < i; ++j) c.eid(nb_c, j, s) = f.eid(nb, j, p);
                 c.eid(nb_c, i, s) = ceid;
             }
+            const Plan& pl = q->plan;
+            for (int a = 0; a < pl.n_anti; ++a) {
+                const int e = pl.anti[a].edge;
+                if (e == i) c.anti_t(anti_off(i + 1), a, s) = ct;
+                else if (e < i) c.anti_t(anti_off(i + 1), a, s) = f.anti_t(anti_off(i), a, p);
+            }
         }
         __syncwarp();
         setP(i + 1, cp + __popc(kb));
@@ -417,7 +460,7 @@ struct Search {
     __device__ void maybe_donate(int i) {
         const uint32_t np = P(i), off = Off(i), tot = T(i);
         const tm_tuning& tu = q->plan.tune;
-        if (i > tu.split_depth || tot - off <= (uint32_t)tu.split_min) return;
+        if (i > tu.split_depth || tot - off <= (uint32_t)tu.split_min || q->plan.n_anti) return;
         if ((++polls & 15u) != 1u) return;      // look at the idle count every 16th step
         int idle = 0;
         if (lane == 0) idle = *(volatile int*)&ctrl->idle;
@@ -510,6 +553,8 @@ struct Search {
                 if (pl.elabel0 >= 0) ok &= g.elabel[r] == (uint8_t)pl.elabel0;
                 if (pl.nl_x0 >= 0) ok &= g.nlabel[s] == (uint8_t)pl.nl_x0;
                 if (pl.nl_y0 >= 0) ok &= g.nlabel[d] == (uint8_t)pl.nl_y0;
+                if (ok && pl.anti_mask0)
+                    ok = anti_clear(pl.anti_mask0, 0, Frame{wbase}, 0, 0, s, d, tt, tt, 0);
             }
             if (STATS && lane == 0) acc.w[W_ROOTS] += (r1 - rb < 32ull) ? (unsigned long long)(r1 - rb) : 32ull;
             if (k == 1) {
@@ -546,6 +591,8 @@ struct Search {
                     c.len(sl) = clen;
                     c.root(sl) = (uint32_t)r;
                     if (MODE == MODE_FILL) c.eid(2, 0, sl) = (int32_t)r;
+                    for (int a = 0; a < pl.n_anti; ++a)
+                        if (pl.anti[a].edge == 0) c.anti_t(anti_off(1), a, sl) = tt;
                 }
                 __syncwarp();
                 setP(1, cp + __popc(kb));

@@ -96,10 +96,23 @@ struct LevelPlan {
     int16_t nl1;       // FREE: label of the second new node (y_i)
     int8_t nx_a;       // SuccKind giving the window start of the list used by EXT / CLOSE(out) levels
     int8_t nx_b;       // SuccKind for the in-list option of a CLOSE level
+    uint8_t anti_mask; // anti-edges whose nodes and attached edge are all bound once edge i is
+    uint8_t pad1;
     int32_t frame_off;       // byte offset of this level's frame in a warp's shared block (count)
     int32_t frame_off_fill;  // same, enumerate-fill layout (frames also carry edge ids)
-    int32_t pad2;
+    int32_t anti_row_off;    // byte offset of the anti-edge time rows within this level's frame
+    int32_t anti_row_off_fill;
     int64_t gap;             // t_i - t_{i-1} bound (INT64_MAX = none)
+};
+
+// One temporal anti-edge (paper Section 2.1, Section 5.4.3), checked at the
+// level where its two nodes and its attached edge are all bound.
+struct AntiPlan {
+    int8_t xs, ys;     // slots of the absent edge's endpoints
+    int8_t edge;       // attached motif edge i
+    int8_t same_pair;  // the attached edge joins the same two nodes (exclude it)
+    int32_t pad;
+    int64_t delta;     // window [t(e_i), t(e_i) + delta]
 };
 
 constexpr int FCAP = 64;          // parents per frame (two per lane)
@@ -112,20 +125,25 @@ struct Plan {
     int32_t warp_smem_fill;        // same, enumerate fill
     tm_tuning tune;
     uint64_t shape_hash;
+    int32_t n_anti;
+    uint8_t anti_mask0;            // anti-edges checked when the root binds edge 0
+    uint8_t pad1[3];
+    AntiPlan anti[TM_MAX_ANTI];
     LevelPlan lv[TM_MAX_EDGES];    // lv[i] for i = 1..k-1
 };
 
 // Frame field offsets (bytes, relative to frame start), FCAP entries each.
-//   tprev i64, tend i64, beg u32 (bit 31: in-list), len u32, root u32,
-//   node[nb] i32, eid[i] i32 (enumerate only)
+//   tprev i64, tend i64, beg u32 (bits 31/30: list kind), len u32, root u32,
+//   node[nb] i32, eid[i] i32 (enumerate only), anti_t[n_anti] i64 (motifs with
+//   anti-edges: time of each anti-edge's attached edge once bound)
 constexpr int F_TPREV = 0;
 constexpr int F_TEND = F_TPREV + 8 * FCAP;
 constexpr int F_BEG = F_TEND + 8 * FCAP;
 constexpr int F_LEN = F_BEG + 4 * FCAP;
 constexpr int F_ROOT = F_LEN + 4 * FCAP;
 constexpr int F_NODE = F_ROOT + 4 * FCAP;
-inline int frame_bytes(int nb, int level, bool with_eids) {
-    return F_NODE + 4 * FCAP * (nb + (with_eids ? level : 0));
+inline int frame_bytes(int nb, int level, bool with_eids, int n_anti = 0) {
+    return F_NODE + 4 * FCAP * (nb + (with_eids ? level : 0)) + 8 * FCAP * n_anti;
 }
 constexpr int WARP_HDR = 128;      // per-warp header: level cursors
 

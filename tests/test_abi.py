@@ -53,7 +53,7 @@ def test_struct_layouts_match_header():
     """Sizes of the ABI structs as the binding sees them (C layout rules)."""
     import paper_2310_02800_gb300 as tmg
     assert ctypes.sizeof(tmg._Edges) == 8 * 2 + 8 * 5 + 8
-    assert ctypes.sizeof(tmg._Motif) == 4 + 4 + 8 + 8 + 8 + 7 * 8 + 16 + 16
+    assert ctypes.sizeof(tmg._Motif) == 4 + 4 + 8 + 8 + 8 + 7 * 8 + 16 + 16 + 4 + 4 * 3 + 4 * 8
     assert ctypes.sizeof(tmg.Tuning) == 16
     assert ctypes.sizeof(tmg._Work) == 8 * (1 + 8 + 8 + 1 + 1)
 

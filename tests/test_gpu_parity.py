@@ -297,3 +297,41 @@ def test_bounded_wait_reports_timeout_and_context_survives(tmg):
         q.count()
     assert ei.value.status == tmg.E_TIMEOUT
     assert q.count() == og.count(mo)
+
+
+ANTI_MOTIFS = [
+    ([(0, 1), (1, 2), (2, 0)], [(0, 2, 0, 300)]),
+    ([(0, 1), (1, 2), (2, 0)], [(1, 0, 1, 500), (2, 1, 2, 200)]),
+    ([(0, 1), (1, 0)], [(0, 1, 0, 400)]),
+    ([(0, 1), (0, 2), (0, 3)], [(1, 2, 2, 600)]),
+    ([(0, 1), (1, 2)], [(2, 0, 0, 0)]),
+    ([(0, 1), (1, 2), (2, 3), (3, 0)], [(0, 2, 1, 150), (3, 1, 0, 250)]),   # attached to an earlier edge
+    ([(0, 1)], [(1, 0, 0, 300)]),
+]
+
+
+def test_anti_edges(tmg):
+    """Temporal anti-edges: counts, per-root counts and enumeration equal the oracle's, on a dense
+    multigraph (pair-list lookups) and a sparse one (short lists)."""
+    rng = np.random.default_rng(31)
+    for n, m, tmax in ((40, 6000, 30_000), (400, 6000, 200_000)):
+        src = rng.integers(0, n, m).astype(np.int32)
+        dst = rng.integers(0, n, m).astype(np.int32)
+        t = rng.integers(0, tmax, m).astype(np.int64)
+        og = oracle.Graph(n, src, dst, t)
+        gg = tmg.Graph.load(n, src, dst, t)
+        for edges, anti in ANTI_MOTIFS:
+            delta = 400 if len(edges) <= 3 else 200
+            mo = synth.Motif(edges, delta, anti=anti, name=f"{edges} anti {anti}")
+            check_query(tmg, gg, og, mo, enum_cap="all")
+
+
+def test_anti_edge_walkthrough_golden(tmg):
+    import json, os
+    spec = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "walkthrough.json")))
+    for case in spec["cases"]:
+        e = np.array(case["edges"], np.int64)
+        gg = tmg.Graph.load(int(e[:, :2].max()) + 1, e[:, 0].astype(np.int32), e[:, 1].astype(np.int32), e[:, 2])
+        mo = synth.Motif([tuple(x) for x in case["motif"]], case["delta"], case["gaps"],
+                         anti=[tuple(a) for a in case.get("anti", [])])
+        assert gg.compile(mo).count() == case["expected_count"], case["reason"]
