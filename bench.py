@@ -324,6 +324,8 @@ def main():
                      "alg_bytes_per_step": int(b_low),
                      "kernel_ms_per_step": {"count": count_ms, "enum_count_pass": enum_count_ms, "fill": fill_ms}},
     }
+    if rank == 0 and not args.no_extras:
+        line["ablation"] = ablation_leg(queries, qs, stream)
     if rank == 0 and not args.no_extras and not count_only:
         line["e2e"] = e2e_leg(args, g, queries, dev)
         line["batched"] = batched_leg(gg, dev, stream)
@@ -331,6 +333,19 @@ def main():
         line["cpu_baseline"] = cpu_leg(g, queries, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def ablation_leg(queries, qs, stream):
+    """Same counts with the paper's thread-per-tree baseline design (Section 3.2) on this GPU."""
+    out = {}
+    for mo, q in zip(queries, qs):
+        c0 = q.count(stream=stream)
+        ms_ours = q.last_ms()[0]
+        c1, ms_base = q.count_baseline(stream=stream)
+        assert c1 == c0
+        out[mo.name] = {"search_kernel_ms": round(ms_ours, 4), "baseline_kernel_ms": round(ms_base, 4),
+                        "speedup": round(ms_base / max(ms_ours, 1e-9), 2)}
+    return out
 
 
 def e2e_leg(args, g, queries, dev):

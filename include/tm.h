@@ -209,6 +209,15 @@ tm_status tm_query_inject_fault(tm_query* q, int kind);
  * since it was loaded, over all threads. */
 uint64_t tm_kernel_launches(void);
 
+/* Ablation: count with the paper's GPU baseline design (Section 3.2) -- one
+ * thread per search tree following Algorithm 1, candidate lists located by
+ * binary search at every visit (no cached ranges), structural checks by
+ * scanning the motif-to-graph map, no work sharing -- on this library's graph
+ * layout.  Same result as tm_count (motifs without anti-edges; TM_E_INVALID
+ * otherwise).  kernel_ms (nullable, host) receives the kernel's device time.
+ * Synchronises the stream. */
+tm_status tm_count_baseline(tm_graph* g, tm_query* q, void* stream, uint64_t* total, double* kernel_ms);
+
 /* Pick tm_tuning for this query's shape by timing candidate settings on the
  * resident graph; the choice is cached per shape in the graph and applied to
  * q.  tuned (nullable, host) receives it. */

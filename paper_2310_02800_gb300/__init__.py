@@ -90,6 +90,7 @@ _SIGS = [
     ("tm_count_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     ("tm_count_batch_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     ("tm_autotune", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Tuning)]),
+    ("tm_count_baseline", ctypes.c_int, [_P, _P, _P, _U64P, ctypes.POINTER(ctypes.c_double)]),
     ("tm_query_work", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_Work)]),
     ("tm_serve_start", ctypes.c_int, [_P, ctypes.POINTER(_ServeCfg), _PP]),
     ("tm_serve_submit", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_uint64, _U64P]),
@@ -303,6 +304,12 @@ class Query:
         st = _check(lib().tm_enumerate(self.graph._h, self._h, _stream_ptr(stream), _ptr(out), cap,
                                        ctypes.byref(nw), ctypes.byref(tot)), allow=(OK, E_TRUNCATED))
         return nw.value, tot.value, st == E_TRUNCATED
+
+    def count_baseline(self, stream=None):
+        """(count, kernel ms) with the paper's thread-per-tree GPU baseline design (ablation)."""
+        tot, ms = ctypes.c_uint64(), ctypes.c_double()
+        _check(lib().tm_count_baseline(self.graph._h, self._h, _stream_ptr(stream), ctypes.byref(tot), ctypes.byref(ms)))
+        return tot.value, ms.value
 
     def profile(self, enable=True):
         _check(lib().tm_query_profile(self._h, 1 if enable else 0))

@@ -280,6 +280,7 @@ static void apply_cached_tuning(tm_graph* g, tm_query* q) {
 }
 
 const tm_graph* query_graph(const tm_query* q) { return q->g; }
+const tm_motif* query_motif(const tm_query* q) { return &q->motif; }
 
 void query_plan(tm_query* q, Plan* out) {
     apply_cached_tuning(q->g, q);

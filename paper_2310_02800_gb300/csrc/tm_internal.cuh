@@ -227,8 +227,9 @@ void drop_batches(const tm_graph* g);
 // The query's plan with the graph's cached tuning for its shape applied.
 void query_plan(tm_query* q, Plan* out);
 
-// The graph a query was compiled for.
+// The graph a query was compiled for, and the motif it was compiled from.
 const tm_graph* query_graph(const tm_query* q);
+const tm_motif* query_motif(const tm_query* q);
 
 tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len, uint64_t chunks,
                           uint64_t task_cap);

@@ -335,3 +335,20 @@ def test_anti_edge_walkthrough_golden(tmg):
         mo = synth.Motif([tuple(x) for x in case["motif"]], case["delta"], case["gaps"],
                          anti=[tuple(a) for a in case.get("anti", [])])
         assert gg.compile(mo).count() == case["expected_count"], case["reason"]
+
+
+def test_baseline_ablation_kernel_counts(tmg):
+    """The thread-per-tree baseline kernel (ablation) gives the oracle's counts too."""
+    rng = np.random.default_rng(8)
+    n, m = 40, 5000
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    t = rng.integers(0, 30_000, m).astype(np.int64)
+    el = rng.integers(0, 2, m).astype(np.uint8)
+    og = oracle.Graph(n, src, dst, t, el)
+    gg = tmg.Graph.load(n, src, dst, t, el)
+    for edges in MOTIFS:
+        mo = synth.Motif(edges, 300 if len(edges) <= 3 else 120, name=str(edges))
+        assert gg.compile(mo).count_baseline()[0] == og.count(mo), edges
+    mo = synth.Motif([(0, 1), (1, 2), (2, 0)], 300, [100, 150], elabel=[1, -1, 0])
+    assert gg.compile(mo).count_baseline()[0] == og.count(mo)
