@@ -153,6 +153,8 @@ tm_status tm_graph_edge_perm(const tm_graph* g, int64_t* out_perm);
  * evaluate.  The query owns its scratch memory: one query must not run on two
  * streams at the same time. */
 tm_status tm_query_compile(const tm_graph* g, const tm_motif* motif, tm_query** out);
+/* A graph must outlive the queries and servers made from it; a query may be
+ * freed before or after its graph. */
 tm_status tm_query_free(tm_query* q);
 
 /* Override / read the execution knobs of a query. */

@@ -255,6 +255,7 @@ using namespace tmg;
 
 struct tm_query {
     tm_graph* g = nullptr;
+    int device = 0;          // the graph's device (kept here: freeing needs no graph access)
     tm_motif motif{};
     Plan plan{};
     bool explicit_tuning = false;
@@ -353,6 +354,7 @@ extern "C" tm_status tm_query_compile(const tm_graph* g, const tm_motif* m, tm_q
     if (s != TM_OK) return s;
     tm_query* q = new tm_query();
     q->g = const_cast<tm_graph*>(g);
+    q->device = g->device;
     q->motif = *m;
     q->plan = p;
     *out = q;
@@ -361,7 +363,7 @@ extern "C" tm_status tm_query_compile(const tm_graph* g, const tm_motif* m, tm_q
 
 extern "C" tm_status tm_query_free(tm_query* q) {
     if (!q) return TM_OK;
-    cudaSetDevice(q->g->device);
+    cudaSetDevice(q->device);
     scratch_free(&q->scratch);
     for (auto& e : q->ev)
         if (e) cudaEventDestroy(e);
@@ -384,7 +386,7 @@ extern "C" tm_status tm_query_set_tuning(tm_query* q, const tm_tuning* t) {
 
 extern "C" tm_status tm_query_profile(tm_query* q, int enable) {
     if (!q) { set_error("null query"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(q->g->device));
+    TM_ENTER(q->device);
     if (enable && !q->ev[0])
         for (auto& e : q->ev) TM_CUDA(cudaEventCreate(&e));
     q->profile = enable != 0;
@@ -417,7 +419,7 @@ extern "C" tm_status tm_count_roots(tm_graph* g, tm_query* q, int64_t rb, int64_
                                     uint64_t* per_root_dev) {
     if (!g || !q || !total || q->g != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
     if (rb < 0 || re < rb || re > g->v.m) { set_error("root range out of [0, n_edges]"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     apply_cached_tuning(g, q);
     cudaStream_t st = (cudaStream_t)stream;
     if (re == rb) {
@@ -439,7 +441,7 @@ extern "C" tm_status tm_count(tm_graph* g, tm_query* q, void* stream, uint64_t* 
 
 extern "C" tm_status tm_query_work(tm_graph* g, tm_query* q, void* stream, tm_work* out) {
     if (!g || !q || !out || q->g != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     apply_cached_tuning(g, q);
     cudaStream_t st = (cudaStream_t)stream;
     memset(out, 0, sizeof *out);
@@ -458,7 +460,7 @@ extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_
         set_error("null or mismatched argument");
         return TM_E_INVALID;
     }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     apply_cached_tuning(g, q);
     cudaStream_t st = (cudaStream_t)stream;
     const uint64_t m = (uint64_t)g->v.m;
@@ -552,7 +554,7 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
     if (!g || !qs || nq < 1 || nq > 4096 || !totals) { set_error("bad batch arguments"); return TM_E_INVALID; }
     for (int j = 0; j < nq; ++j)
         if (!qs[j] || qs[j]->g != g) { set_error("null or mismatched query in batch"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (g->v.m == 0) {
         for (int j = 0; j < nq; ++j) totals[j] = 0;
@@ -616,7 +618,7 @@ void tmg::drop_batches(const tm_graph* g) {
 
 extern "C" tm_status tm_autotune(tm_graph* g, tm_query* q, void* stream, tm_tuning* tuned) {
     if (!g || !q || q->g != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     const uint64_t m = (uint64_t)g->v.m;
     tm_tuning best = q->plan.tune;

@@ -66,6 +66,9 @@ __global__ void baseline_kernel(const __grid_constant__ GraphView g, const __gri
         int lvl = 1;
         bool fresh = true;          // entering lvl for the first time (cursor at list start)
         while (lvl >= 1) {
+            // RollbackDataStructures: forget what this level mapped for its previous candidate
+            for (int j = 0; j < q.n_nodes; ++j)
+                if (owner[j] == lvl) { map[j] = -1; owner[j] = -1; }
             const int x = q.esrc[lvl], y = q.edst[lvl];
             const int32_t uG = map[x], vG = map[y];
             const int64_t tprev = g.t[stack_e[lvl - 1]];
@@ -88,9 +91,6 @@ __global__ void baseline_kernel(const __grid_constant__ GraphView g, const __gri
             }
             uint32_t p = bl_upper(tarr, lo, hi, tprev);
             if (!fresh) p = max(p, cur[lvl] + 1);      // continue after the candidate just explored
-            // unmap what this level mapped before (RollbackDataStructures)
-            for (int j = 0; j < q.n_nodes; ++j)
-                if (owner[j] == lvl) { map[j] = -1; owner[j] = -1; }
             bool advanced = false;
             for (; p < hi; ++p) {
                 const int64_t te = __ldg(tarr + p);
@@ -144,7 +144,7 @@ extern "C" tm_status tm_count_baseline(tm_graph* g, tm_query* q, void* stream, u
     if (!g || !q || !total || query_graph(q) != g) { set_error("null or mismatched argument"); return TM_E_INVALID; }
     const tm_motif* m = query_motif(q);
     if (m->n_anti > 0) { set_error("the baseline kernel has no anti-edges"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     BaselineMotif bm;
     memset(&bm, 0, sizeof bm);

@@ -409,7 +409,7 @@ extern "C" tm_status tm_graph_load(const tm_edges* e, int device, void* stream, 
     int ndev = 0;
     TM_CUDA(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) { set_error("bad device"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(device));
+    TM_ENTER(device);
     tm_graph* g = new tm_graph();
     g->device = device;
     cudaDeviceProp prop;
@@ -444,7 +444,7 @@ extern "C" tm_status tm_graph_info(const tm_graph* g, int64_t* n_nodes, int64_t*
 extern "C" tm_status tm_graph_edge_perm(const tm_graph* g, int64_t* out_perm) {
     if (!g || (!out_perm && g->v.m > 0)) { set_error("null argument"); return TM_E_INVALID; }
     if (g->v.m == 0) return TM_OK;
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     std::vector<int32_t> tmp((size_t)g->v.m);
     TM_CUDA(cudaMemcpy(tmp.data(), g->perm, g->v.m * 4, cudaMemcpyDeviceToHost));
     for (int64_t i = 0; i < g->v.m; ++i) out_perm[i] = tmp[i];

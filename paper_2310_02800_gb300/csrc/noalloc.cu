@@ -78,7 +78,7 @@ extern "C" tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, in
                   "], the capacity of its static scratch");
         return TM_E_INVALID;
     }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* base = nullptr;
     tm_status s = scratch_address(g->device, &base);

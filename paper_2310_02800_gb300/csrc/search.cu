@@ -42,7 +42,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t INLIST = 0x80000000u;    // window in an in-list
 constexpr uint32_t PAIRLIST = 0x40000000u;  // window in the (neighbour, time)-ordered out-list
 constexpr uint32_t POSMASK = 0x3FFFFFFFu;
-constexpr uint32_t PAIR_MIN_DEG = 48;       // closing lookups on shorter lists scan the time window
+constexpr uint32_t PAIR_MIN_DEG = 1024;     // closing lookups on shorter lists scan the time window
+constexpr uint32_t PAIR_MIN_WINDOW = 768;   // ... and so do windows shorter than this
 constexpr uint64_t WAIT_NS = 20ull * 1000 * 1000 * 1000;      // idle-wait deadline
 constexpr uint64_t READY_NS = 2ull * 1000 * 1000 * 1000;      // publish-wait deadline
 
@@ -241,9 +242,19 @@ struct Search {
                 int32_t u = slot(lp.a), w = slot(lp.b);
                 uint32_t u0 = __ldg(g.off[0] + u), u1 = __ldg(g.off[0] + u + 1);
                 uint32_t w0 = __ldg(g.off[1] + w), w1 = __ldg(g.off[1] + w + 1);
-                if (!STATS && min(u1 - u0, w1 - w0) >= PAIR_MIN_DEG) {
-                    // both lists are long: take the u -> w edges straight from the
-                    // pair-ordered out-list of u (neighbour range, then time window)
+                if (u1 - u0 <= w1 - w0) { dir = 0; lo = u0; hi = u1; nx = lp.nx_a; }
+                else { dir = 1; lo = w0; hi = w1; nx = lp.nx_b; }
+                if (!STATS && hi - lo >= PAIR_MIN_DEG) {
+                    // a long list: if its time window is long too, take the u -> w
+                    // edges straight from u's pair-ordered out-list instead of
+                    // scanning the window for one neighbour
+                    const int64_t* ta = g.at[dir];
+                    uint32_t b0 = nx >= 0 ? __ldg(g.nxt[nx] + prev_e) : upper_bound_t(ta, lo, hi, tprev);
+                    uint32_t e0 = (b0 < hi) ? gallop_end(ta, b0, hi, lim) : b0;
+                    if (e0 - b0 < PAIR_MIN_WINDOW) {
+                        beg_out = b0 | (dir ? INLIST : 0u);
+                        return e0 - b0;
+                    }
                     uint32_t ps = lower_bound_i32(g.pnbr, u0, u1, w);
                     uint32_t pe = lower_bound_i32(g.pnbr, ps, u1, w + 1);
                     uint32_t pb = upper_bound_t(g.pt, ps, pe, tprev);
@@ -251,8 +262,6 @@ struct Search {
                     beg_out = pb | PAIRLIST;
                     return pz - pb;
                 }
-                if (u1 - u0 <= w1 - w0) { dir = 0; lo = u0; hi = u1; nx = lp.nx_a; }
-                else { dir = 1; lo = w0; hi = w1; nx = lp.nx_b; }
             } else {
                 dir = kind == EXT_IN ? 1 : 0;
                 int32_t v = slot(lp.a);

@@ -273,7 +273,7 @@ void scheduler(tm_server* s) {
 
 extern "C" tm_status tm_serve_start(tm_graph* g, const tm_serve_cfg* cfg, tm_server** out) {
     if (!g || !out) { set_error("null argument"); return TM_E_INVALID; }
-    TM_CUDA(cudaSetDevice(g->device));
+    TM_ENTER(g->device);
     tm_server* s = new tm_server();
     s->g = g;
     s->cfg = cfg ? *cfg : tm_serve_cfg{0, 0, 0};

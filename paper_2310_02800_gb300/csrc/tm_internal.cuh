@@ -20,6 +20,14 @@ void set_error(const std::string& msg);
 void note_launches(uint64_t n);
 tm_status cuda_fail(cudaError_t e, const char* what);
 
+// Select the device and drop any error another library left on this thread,
+// so that only this call's own CUDA errors are reported.
+#define TM_ENTER(dev)                                         \
+    do {                                                      \
+        cudaGetLastError();                                   \
+        TM_CUDA(cudaSetDevice(dev));                          \
+    } while (0)
+
 #define TM_CUDA(call)                                         \
     do {                                                      \
         cudaError_t _e = (call);                              \
