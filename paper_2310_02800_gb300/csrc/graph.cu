@@ -109,6 +109,22 @@ __global__ void list_columns_kernel(const uint32_t* __restrict__ eids, int64_t m
     }
 }
 
+// Successor index by list position (see GraphView::pnx).
+__global__ void successor_by_position_kernel(int64_t m, const int32_t* __restrict__ aeid_out,
+                                             const int32_t* __restrict__ aeid_in, const uint32_t* __restrict__ so_src,
+                                             const uint32_t* __restrict__ so_dst, const uint32_t* __restrict__ si_dst,
+                                             const uint32_t* __restrict__ si_src, uint32_t* __restrict__ p_out_same,
+                                             uint32_t* __restrict__ p_out_dst, uint32_t* __restrict__ p_in_same,
+                                             uint32_t* __restrict__ p_in_src) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t eo = aeid_out[i], ei = aeid_in[i];
+        p_out_same[i] = so_src[eo];
+        p_out_dst[i] = so_dst[eo];
+        p_in_same[i] = si_dst[ei];
+        p_in_src[i] = si_src[ei];
+    }
+}
+
 __global__ void keys_by_perm_kernel(const int32_t* __restrict__ node, const uint32_t* __restrict__ perm, int64_t m,
                                     uint32_t* __restrict__ keys) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
@@ -386,6 +402,16 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
         TM_CUDA(cudaGetLastError());
     }
     for (int j = 0; j < 4; ++j) v.nxt[j] = nx[j];
+    uint32_t* px[4];
+    for (int j = 0; j < 4; ++j) TRY(owned(g, &px[j], m));
+    if (m > 0) {
+        successor_by_position_kernel<<<grid_for(m, sms), 256, 0, st>>>(
+            m, v.aeid[0], v.aeid[1], nx[NX_OUT_SRC], nx[NX_OUT_DST], nx[NX_IN_DST], nx[NX_IN_SRC], px[0], px[1], px[2],
+            px[3]);
+        note_launches(1);
+        TM_CUDA(cudaGetLastError());
+    }
+    for (int j = 0; j < 4; ++j) v.pnx[j] = px[j];
     TM_CUDA(cudaStreamSynchronize(st));
     return TM_OK;
 }

@@ -221,8 +221,26 @@ struct Search {
     // window's lower end comes from the successor index when the list belongs
     // to an endpoint of prev_e, else from a binary search; the upper end from
     // a galloping search.  Returns len; beg gets bit 31 for in-lists.
+    // The edge just bound sits at position cpos of list cdir (0 out-list, 1 in-list,
+    // 2 the edge list itself, 3 a pair-ordered list); prev_e is its edge id when
+    // already loaded, else -1.  Successor-index lookups read the position-indexed
+    // copy when it covers the continuation, else the edge-indexed one.
+    __device__ uint32_t successor(int nx, int cdir, uint32_t cpos, int32_t prev_e) const {
+        if (cdir == 0 && nx == NX_OUT_SRC) return __ldg(g.pnx[0] + cpos);
+        if (cdir == 0 && nx == NX_OUT_DST) return __ldg(g.pnx[1] + cpos);
+        if (cdir == 1 && nx == NX_IN_DST) return __ldg(g.pnx[2] + cpos);
+        if (cdir == 1 && nx == NX_IN_SRC) return __ldg(g.pnx[3] + cpos);
+        return __ldg(g.nxt[nx] + edge_at(cdir, cpos, prev_e));
+    }
+    __device__ int32_t edge_at(int cdir, uint32_t cpos, int32_t prev_e) const {
+        if (prev_e >= 0) return prev_e;
+        if (cdir == 0 || cdir == 1) return __ldg(g.aeid[cdir] + cpos);
+        if (cdir == 3) return __ldg(g.peid + cpos);
+        return (int32_t)cpos;
+    }
+
     __device__ uint32_t locate(int lv_i, Frame pf, int ps, int nb, int32_t n0, int32_t n1, int32_t prev_e,
-                               int64_t tprev, int64_t tend, uint32_t& beg_out) {
+                               int cdir, uint32_t cpos, int64_t tprev, int64_t tend, uint32_t& beg_out) {
         const LevelPlan& lp = q->plan.lv[lv_i];
         auto slot = [&](int s) -> int32_t { return s < nb ? pf.node(s, ps) : (s == nb ? n0 : n1); };
         int64_t lim = min(tend, sat_add(tprev, lp.gap));
@@ -232,7 +250,7 @@ struct Search {
         if (kind == FREE) {
             tarr = g.t;
             hi = (uint32_t)g.m;
-            b = gallop_end(tarr, (uint32_t)prev_e + 1u, hi, tprev);
+            b = gallop_end(tarr, (uint32_t)edge_at(cdir, cpos, prev_e) + 1u, hi, tprev);
             if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi);
         } else {
             int dir, nx;
@@ -249,7 +267,7 @@ struct Search {
                     // edges straight from u's pair-ordered out-list instead of
                     // scanning the window for one neighbour
                     const int64_t* ta = g.at[dir];
-                    uint32_t b0 = nx >= 0 ? __ldg(g.nxt[nx] + prev_e) : upper_bound_t(ta, lo, hi, tprev);
+                    uint32_t b0 = nx >= 0 ? successor(nx, cdir, cpos, prev_e) : upper_bound_t(ta, lo, hi, tprev);
                     uint32_t e0 = (b0 < hi) ? gallop_end(ta, b0, hi, lim) : b0;
                     if (e0 - b0 < PAIR_MIN_WINDOW) {
                         beg_out = b0 | (dir ? INLIST : 0u);
@@ -271,7 +289,7 @@ struct Search {
             }
             tarr = g.at[dir];
             flag = dir ? INLIST : 0u;
-            b = nx >= 0 ? __ldg(g.nxt[nx] + prev_e) : upper_bound_t(tarr, lo, hi, tprev);
+            b = nx >= 0 ? successor(nx, cdir, cpos, prev_e) : upper_bound_t(tarr, lo, hi, tprev);
             if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi - lo);
         }
         uint32_t e = (b < hi) ? gallop_end(tarr, b, hi, lim) : b;
@@ -374,12 +392,15 @@ struct Search {
         int64_t ct = 0;
         bool ok = act;
         const int kind = lp.kind;
-        // the candidate's edge id: written by enumeration, read by edge labels and
-        // by the next level's successor-index lookup
-        const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0 || i < k - 1;
+        // the candidate's edge id: written by enumeration and read by edge labels;
+        // the next level's successor lookup loads it only if it needs it
+        const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0;
+        int cdir = 2;
+        uint32_t pos = 0;
         if (act) {
             uint32_t bw = f.beg(p);
-            uint32_t pos = (bw & POSMASK) + within;
+            pos = (bw & POSMASK) + within;
+            cdir = (bw & PAIRLIST) ? 3 : (kind == FREE ? 2 : ((bw & INLIST) ? 1 : 0));
             if (bw & PAIRLIST) {
                 // closing edge from the pair-ordered list: structure holds by construction
                 ct = __ldg(g.pt + pos);
@@ -424,7 +445,7 @@ struct Search {
         int64_t tend = 0;
         if (ok) {
             tend = f.tend(p);
-            clen = locate(i + 1, f, p, nb, n0, n1, ceid, ct, tend, cbeg);
+            clen = locate(i + 1, f, p, nb, n0, n1, ceid, cdir, pos, ct, tend, cbeg);
         }
         if (STATS) {
             unsigned b = __ballot_sync(FULL, ok);
@@ -574,7 +595,7 @@ struct Search {
             int64_t tend = 0;
             if (ok) {
                 tend = sat_add(tt, pl.delta);
-                clen = locate(1, Frame{wbase}, 0, 0, s, d, (int32_t)r, tt, tend, cbeg);
+                clen = locate(1, Frame{wbase}, 0, 0, s, d, (int32_t)r, 2, (uint32_t)r, tt, tend, cbeg);
             }
             if (STATS) {
                 unsigned b = __ballot_sync(FULL, ok);

@@ -54,6 +54,10 @@ struct GraphView {
     // successor index, by edge id e = (u, v, t): first position with time > t in
     // out(u), in(v), out(v), in(u) (absolute positions in the list columns)
     const uint32_t* nxt[4];
+    // the same, indexed by list position for the common continuations: [0] out-list
+    // entry -> next later in that out-list, [1] out-list entry -> out(its neighbour),
+    // [2] in-list entry -> next later in that in-list, [3] in-list entry -> in(its neighbour)
+    const uint32_t* pnx[4];
     // out-lists again, ordered by (neighbour, time) within each node (offsets off[0]):
     // the edges u -> v form one contiguous, time-ordered range
     const int32_t* pnbr;
