@@ -79,6 +79,21 @@ __device__ __forceinline__ uint32_t gallop_end(const int64_t* __restrict__ t, ui
     return upper_bound_t(t, a, b, lim);
 }
 
+// End of a time window that starts at beg: the first index in [beg, hi) with
+// t[idx] > lim.  Windows are mostly a few entries long, so the first four
+// entries are read at once (independent loads, one round trip) before any
+// galloping.
+__device__ __forceinline__ uint32_t window_end(const int64_t* __restrict__ t, uint32_t beg, uint32_t hi, int64_t lim) {
+    const uint32_t n = min(hi - beg, 4u);
+    const int64_t t0 = n > 0 ? __ldg(t + beg) : INT64_MAX;
+    const int64_t t1 = n > 1 ? __ldg(t + beg + 1) : INT64_MAX;
+    const int64_t t2 = n > 2 ? __ldg(t + beg + 2) : INT64_MAX;
+    const int64_t t3 = n > 3 ? __ldg(t + beg + 3) : INT64_MAX;
+    const uint32_t c = (t0 <= lim) + (t1 <= lim) + (t2 <= lim) + (t3 <= lim);
+    if (c < 4u) return beg + c;
+    return gallop_end(t, beg + 4u, hi, lim);
+}
+
 __device__ __forceinline__ uint32_t ceil_log2p1(uint32_t x) { return 32 - __clz(x); }  // ceil(log2(x+1))
 
 // first index in [lo, hi) with a[idx] >= x
@@ -268,7 +283,7 @@ struct Search {
                     // scanning the window for one neighbour
                     const int64_t* ta = g.at[dir];
                     uint32_t b0 = nx >= 0 ? successor(nx, cdir, cpos, prev_e) : upper_bound_t(ta, lo, hi, tprev);
-                    uint32_t e0 = (b0 < hi) ? gallop_end(ta, b0, hi, lim) : b0;
+                    uint32_t e0 = (b0 < hi) ? window_end(ta, b0, hi, lim) : b0;
                     if (e0 - b0 < PAIR_MIN_WINDOW) {
                         beg_out = b0 | (dir ? INLIST : 0u);
                         return e0 - b0;
@@ -276,7 +291,7 @@ struct Search {
                     uint32_t ps = lower_bound_i32(g.pnbr, u0, u1, w);
                     uint32_t pe = lower_bound_i32(g.pnbr, ps, u1, w + 1);
                     uint32_t pb = upper_bound_t(g.pt, ps, pe, tprev);
-                    uint32_t pz = (pb < pe) ? gallop_end(g.pt, pb, pe, lim) : pb;
+                    uint32_t pz = (pb < pe) ? window_end(g.pt, pb, pe, lim) : pb;
                     beg_out = pb | PAIRLIST;
                     return pz - pb;
                 }
@@ -292,7 +307,7 @@ struct Search {
             b = nx >= 0 ? successor(nx, cdir, cpos, prev_e) : upper_bound_t(tarr, lo, hi, tprev);
             if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi - lo);
         }
-        uint32_t e = (b < hi) ? gallop_end(tarr, b, hi, lim) : b;
+        uint32_t e = (b < hi) ? window_end(tarr, b, hi, lim) : b;
         beg_out = b | flag;
         return e - b;
     }
