@@ -85,11 +85,12 @@ __device__ __forceinline__ uint32_t gallop_end(const int64_t* __restrict__ t, ui
 // galloping.
 __device__ __forceinline__ uint32_t window_end(const int64_t* __restrict__ t, uint32_t beg, uint32_t hi, int64_t lim) {
     const uint32_t n = min(hi - beg, 4u);
-    const int64_t t0 = n > 0 ? __ldg(t + beg) : INT64_MAX;
-    const int64_t t1 = n > 1 ? __ldg(t + beg + 1) : INT64_MAX;
-    const int64_t t2 = n > 2 ? __ldg(t + beg + 2) : INT64_MAX;
-    const int64_t t3 = n > 3 ? __ldg(t + beg + 3) : INT64_MAX;
-    const uint32_t c = (t0 <= lim) + (t1 <= lim) + (t2 <= lim) + (t3 <= lim);
+    const int64_t t0 = n > 0 ? __ldg(t + beg) : 0;
+    const int64_t t1 = n > 1 ? __ldg(t + beg + 1) : 0;
+    const int64_t t2 = n > 2 ? __ldg(t + beg + 2) : 0;
+    const int64_t t3 = n > 3 ? __ldg(t + beg + 3) : 0;
+    // entries past the list end never count, whatever lim is
+    const uint32_t c = (n > 0 && t0 <= lim) + (n > 1 && t1 <= lim) + (n > 2 && t2 <= lim) + (n > 3 && t3 <= lim);
     if (c < 4u) return beg + c;
     return gallop_end(t, beg + 4u, hi, lim);
 }
