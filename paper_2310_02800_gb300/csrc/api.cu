@@ -324,7 +324,8 @@ static tm_status run_count(tm_graph* g, tm_query* q, uint64_t rb, uint64_t re, c
     if (per_root && re > rb) TM_CUDA(cudaMemsetAsync(per_root, 0, (re - rb) * 8, st));
     if (chunk_counts) TM_CUDA(cudaMemsetAsync(s.chunk_cnt, 0, (nch + 1) * 8, st));
     if (q->profile) TM_CUDA(cudaEventRecord(q->ev[0], st));
-    r = launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block, &s, st,
+    r = launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block,
+                      q->plan.n_anti > 0, &s, st,
                       grid_override, work);
     if (r != TM_OK) return r;
     if (q->profile) TM_CUDA(cudaEventRecord(q->ev[1], st));
@@ -496,7 +497,8 @@ extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_
         qd->total = sc.counters + 1;
         TM_CUDA(cudaMemcpyAsync(sc.head, sc.stage, sc.head_bytes(1), cudaMemcpyHostToDevice, st));
         if (q->profile) TM_CUDA(cudaEventRecord(q->ev[2], st));
-        s = launch_search(g, MODE_FILL, sc.qdev(), 1, q->plan.warp_smem_fill, q->plan.tune.warps_per_block, &sc, st);
+        s = launch_search(g, MODE_FILL, sc.qdev(), 1, q->plan.warp_smem_fill, q->plan.tune.warps_per_block,
+                         q->plan.n_anti > 0, &sc, st);
         if (s != TM_OK) return s;
         if (q->profile) { TM_CUDA(cudaEventRecord(q->ev[3], st)); q->fill_timed = true; }
         TM_CUDA(cudaStreamSynchronize(st));
@@ -513,6 +515,7 @@ namespace tmg {
 // One captured CUDA graph per batch geometry: stage -> kernel -> read back.
 struct BatchExec {
     int nq = 0, warp_smem = 0, warps = 0;
+    bool anti = false;     // some query of the batch has anti-edges
     Scratch scratch;
     cudaGraphExec_t exec = nullptr;
     ~BatchExec() {
@@ -534,7 +537,7 @@ static tm_status capture_batch(tm_graph* g, BatchExec* b, cudaStream_t st) {
     cudaMemcpyAsync(s.head, s.stage, s.head_bytes(b->nq), cudaMemcpyHostToDevice, cs);
     cudaMemsetAsync(s.counters, 0, (size_t)b->nq * 8, cs);
     cudaMemsetAsync(s.ready, 0, s.task_cap, cs);
-    tm_status ls = launch_search(g, MODE_COUNT, s.qdev(), b->nq, b->warp_smem, b->warps, &s, cs);
+    tm_status ls = launch_search(g, MODE_COUNT, s.qdev(), b->nq, b->warp_smem, b->warps, b->anti, &s, cs);
     cudaMemcpyAsync(s.counters_host, s.counters, (size_t)b->nq * 8, cudaMemcpyDeviceToHost, cs);
     cudaMemcpyAsync(s.stage, s.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, cs);
     e = cudaStreamEndCapture(cs, &graph);
@@ -561,21 +564,26 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
         return TM_OK;
     }
     int warp_smem = 16, warps = 0;
+    bool anti = false;
     for (int j = 0; j < nq; ++j) {
         apply_cached_tuning(g, qs[j]);
         warp_smem = std::max(warp_smem, qs[j]->plan.warp_smem);
         warps = std::max(warps, qs[j]->plan.tune.warps_per_block);
+        anti |= qs[j]->plan.n_anti > 0;
     }
     BatchExec* b = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_batch_mu);
         auto& vec = g_batches[g];
         for (auto& p : vec)
-            if (p->nq == nq && p->warp_smem == warp_smem && p->warps == warps) { b = p.get(); break; }
+            if (p->nq == nq && p->warp_smem == warp_smem && p->warps == warps && p->anti == anti) {
+                b = p.get();
+                break;
+            }
         if (!b) {
             vec.emplace_back(new BatchExec());
             b = vec.back().get();
-            b->nq = nq; b->warp_smem = warp_smem; b->warps = warps;
+            b->nq = nq; b->warp_smem = warp_smem; b->warps = warps; b->anti = anti;
         }
     }
     tm_status s = scratch_reserve(&b->scratch, g->device, nq, (uint64_t)nq, 0, DEFAULT_TASK_CAP);

@@ -80,19 +80,9 @@ __device__ __forceinline__ uint32_t gallop_end(const int64_t* __restrict__ t, ui
 }
 
 // End of a time window that starts at beg: the first index in [beg, hi) with
-// t[idx] > lim.  Windows are mostly a few entries long, so the first four
-// entries are read at once (independent loads, one round trip) before any
-// galloping.
+// t[idx] > lim (galloping from beg: O(log of the window length)).
 __device__ __forceinline__ uint32_t window_end(const int64_t* __restrict__ t, uint32_t beg, uint32_t hi, int64_t lim) {
-    const uint32_t n = min(hi - beg, 4u);
-    const int64_t t0 = n > 0 ? __ldg(t + beg) : 0;
-    const int64_t t1 = n > 1 ? __ldg(t + beg + 1) : 0;
-    const int64_t t2 = n > 2 ? __ldg(t + beg + 2) : 0;
-    const int64_t t3 = n > 3 ? __ldg(t + beg + 3) : 0;
-    // entries past the list end never count, whatever lim is
-    const uint32_t c = (n > 0 && t0 <= lim) + (n > 1 && t1 <= lim) + (n > 2 && t2 <= lim) + (n > 3 && t3 <= lim);
-    if (c < 4u) return beg + c;
-    return gallop_end(t, beg + 4u, hi, lim);
+    return gallop_end(t, beg, hi, lim);
 }
 
 __device__ __forceinline__ uint32_t ceil_log2p1(uint32_t x) { return 32 - __clz(x); }  // ceil(log2(x+1))
@@ -144,7 +134,7 @@ struct Acc {             // per-warp accumulators for the current query
     unsigned long long w[W_LEN];   // stats launches; lane-0 values except W_PROBE (per lane)
 };
 
-template <int MODE, bool STATS>
+template <int MODE, bool STATS, bool ANTI>
 struct Search {
     const GraphView& g;
     const QueryDev* __restrict__ qs;
@@ -447,7 +437,7 @@ struct Search {
                 }
             }
             if (lp.elabel >= 0) ok &= g.elabel[ceid] == (uint8_t)lp.elabel;
-            if (ok && lp.anti_mask)
+            if (ANTI && ok && lp.anti_mask)
                 ok = anti_clear(lp.anti_mask, i, f, p, nb, n0, n1, ct, f.tprev(p), anti_off(i));
         }
         uint32_t root = act ? f.root(p) : 0u;
@@ -492,7 +482,7 @@ struct Search {
                 c.eid(nb_c, i, s) = ceid;
             }
             const Plan& pl = q->plan;
-            for (int a = 0; a < pl.n_anti; ++a) {
+            for (int a = 0; ANTI && a < pl.n_anti; ++a) {
                 const int e = pl.anti[a].edge;
                 if (e == i) c.anti_t(anti_off(i + 1), a, s) = ct;
                 else if (e < i) c.anti_t(anti_off(i + 1), a, s) = f.anti_t(anti_off(i), a, p);
@@ -506,7 +496,7 @@ struct Search {
     __device__ void maybe_donate(int i) {
         const uint32_t np = P(i), off = Off(i), tot = T(i);
         const tm_tuning& tu = q->plan.tune;
-        if (i > tu.split_depth || tot - off <= (uint32_t)tu.split_min || q->plan.n_anti) return;
+        if (i > tu.split_depth || tot - off <= (uint32_t)tu.split_min || (ANTI && q->plan.n_anti)) return;
         if ((++polls & 15u) != 1u) return;      // look at the idle count every 16th step
         int idle = 0;
         if (lane == 0) idle = *(volatile int*)&ctrl->idle;
@@ -599,7 +589,7 @@ struct Search {
                 if (pl.elabel0 >= 0) ok &= g.elabel[r] == (uint8_t)pl.elabel0;
                 if (pl.nl_x0 >= 0) ok &= g.nlabel[s] == (uint8_t)pl.nl_x0;
                 if (pl.nl_y0 >= 0) ok &= g.nlabel[d] == (uint8_t)pl.nl_y0;
-                if (ok && pl.anti_mask0)
+                if (ANTI && ok && pl.anti_mask0)
                     ok = anti_clear(pl.anti_mask0, 0, Frame{wbase}, 0, 0, s, d, tt, tt, 0);
             }
             if (STATS && lane == 0) acc.w[W_ROOTS] += (r1 - rb < 32ull) ? (unsigned long long)(r1 - rb) : 32ull;
@@ -637,7 +627,7 @@ struct Search {
                     c.len(sl) = clen;
                     c.root(sl) = (uint32_t)r;
                     if (MODE == MODE_FILL) c.eid(2, 0, sl) = (int32_t)r;
-                    for (int a = 0; a < pl.n_anti; ++a)
+                    for (int a = 0; ANTI && a < pl.n_anti; ++a)
                         if (pl.anti[a].edge == 0) c.anti_t(anti_off(1), a, sl) = tt;
                 }
                 __syncwarp();
@@ -776,13 +766,13 @@ struct Search {
     }
 };
 
-template <int MODE, bool STATS>
+template <int MODE, bool STATS, bool ANTI>
 __global__ void __maxnreg__(56) search_kernel(const __grid_constant__ GraphView g,
                                                      const QueryDev* __restrict__ qs, int nq, int warp_smem,
                                                      Ctrl* ctrl, Task* tasks, uint8_t* ready, uint64_t task_cap) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5;
-    Search<MODE, STATS> s(g, qs, ctrl, tasks, ready, task_cap, smem + (size_t)warp * warp_smem);
+    Search<MODE, STATS, ANTI> s(g, qs, ctrl, tasks, ready, task_cap, smem + (size_t)warp * warp_smem);
     s.run(nq, ctrl->total_chunks);
 }
 
@@ -792,9 +782,14 @@ namespace {
 std::mutex g_cfg_mu;
 std::unordered_map<uint64_t, int> g_blocks_per_sm;   // (device, kernel, warps, smem) -> resident blocks per SM
 
-const void* kernel_of(Mode mode, bool stats) {
-    if (mode == MODE_FILL) return (const void*)search_kernel<MODE_FILL, false>;
-    return stats ? (const void*)search_kernel<MODE_COUNT, true> : (const void*)search_kernel<MODE_COUNT, false>;
+// Kernel instances: count, count with anti-edges, count with work counters
+// (anti-edges included), fill, fill with anti-edges.  Motifs without
+// anti-edges run instances that hold none of their code.
+const void* kernel_of(Mode mode, bool stats, bool anti) {
+    if (mode == MODE_FILL)
+        return anti ? (const void*)search_kernel<MODE_FILL, false, true> : (const void*)search_kernel<MODE_FILL, false, false>;
+    if (stats) return (const void*)search_kernel<MODE_COUNT, true, true>;
+    return anti ? (const void*)search_kernel<MODE_COUNT, false, true> : (const void*)search_kernel<MODE_COUNT, false, false>;
 }
 
 // Resident blocks per SM for one launch shape, computed once per shape.
@@ -819,33 +814,29 @@ LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int
     // keep the block's frames within the 227 KB of shared memory a block may use
     while (c.warps_per_block > 1 && max_warp_smem * c.warps_per_block > 232448) c.warps_per_block--;
     c.smem_bytes = max_warp_smem * c.warps_per_block;
-    int kid = mode == MODE_FILL ? 1 : 0;
-    c.grid = blocks_per_sm(g, kernel_of(mode, false), kid, c.warps_per_block * 32, c.smem_bytes) * g->num_sms;
+    int kid = mode == MODE_FILL ? 4 : 0;
+    c.grid = blocks_per_sm(g, kernel_of(mode, false, false), kid, c.warps_per_block * 32, c.smem_bytes) * g->num_sms;
     return c;
 }
 
 tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, int nq, int max_warp_smem,
-                        int warps_per_block, const Scratch* s, cudaStream_t st, int grid_override, bool stats) {
+                        int warps_per_block, bool anti, const Scratch* s, cudaStream_t st, int grid_override,
+                        bool stats) {
     LaunchCfg c = search_launch_cfg(g, mode, max_warp_smem, warps_per_block);
     int grid = grid_override > 0 ? grid_override : c.grid;
-    dim3 block(c.warps_per_block * 32);
-    if (mode == MODE_COUNT) {
-        if (stats) {
-            blocks_per_sm(g, kernel_of(MODE_COUNT, true), 2, c.warps_per_block * 32, c.smem_bytes);
-            search_kernel<MODE_COUNT, true><<<grid, block, c.smem_bytes, st>>>(
-                g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
-            note_launches(1);
-        } else {
-            search_kernel<MODE_COUNT, false><<<grid, block, c.smem_bytes, st>>>(
-                g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
-            note_launches(1);
-        }
-    } else {
-        search_kernel<MODE_FILL, false><<<grid, block, c.smem_bytes, st>>>(
-            g->v, qdev_dev, nq, max_warp_smem, s->ctrl(), s->tasks, s->ready, s->task_cap);
-        note_launches(1);
-    }
-    TM_CUDA(cudaGetLastError());
+    if (mode == MODE_FILL) stats = false;
+    const void* fn = kernel_of(mode, stats, anti);
+    // the instance's shared-memory limit (set once per launch shape)
+    blocks_per_sm(g, fn, (mode == MODE_FILL ? 4 : 0) + (stats ? 2 : 0) + (anti ? 1 : 0), c.warps_per_block * 32,
+                  c.smem_bytes);
+    GraphView v = g->v;
+    Ctrl* ctrl = s->ctrl();
+    Task* tasks = s->tasks;
+    uint8_t* ready = s->ready;
+    uint64_t cap = s->task_cap;
+    void* args[] = {&v, (void*)&qdev_dev, &nq, &max_warp_smem, &ctrl, &tasks, &ready, &cap};
+    TM_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(c.warps_per_block * 32), args, (size_t)c.smem_bytes, st));
+    note_launches(1);
     return TM_OK;
 }
 

@@ -257,8 +257,10 @@ struct LaunchCfg {
 
 // Launch the persistent search over nq queries (qdev already on the device).
 // Ctrl (incl. total_chunks) and qdev must already be initialised on the stream.
+// `anti` selects the kernel instance that checks anti-edges: it must be true
+// when any of the nq queries has one.
 tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, int nq,
-                        int max_warp_smem, int warps_per_block,
+                        int max_warp_smem, int warps_per_block, bool anti,
                         const Scratch* s, cudaStream_t st, int grid_override = 0, bool stats = false);
 
 LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int warps_per_block);
