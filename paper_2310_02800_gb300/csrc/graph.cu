@@ -109,13 +109,14 @@ __global__ void list_columns_kernel(const uint32_t* __restrict__ eids, int64_t m
     }
 }
 
-// Successor index by list position (see GraphView::pnx).
+// Successor index by list position (see GraphView::pnx): the words of the
+// edge at each list position.
 __global__ void successor_by_position_kernel(int64_t m, const int32_t* __restrict__ aeid_out,
-                                             const int32_t* __restrict__ aeid_in, const uint32_t* __restrict__ so_src,
-                                             const uint32_t* __restrict__ so_dst, const uint32_t* __restrict__ si_dst,
-                                             const uint32_t* __restrict__ si_src, uint32_t* __restrict__ p_out_same,
-                                             uint32_t* __restrict__ p_out_dst, uint32_t* __restrict__ p_in_same,
-                                             uint32_t* __restrict__ p_in_src) {
+                                             const int32_t* __restrict__ aeid_in, const uint2* __restrict__ so_src,
+                                             const uint2* __restrict__ so_dst, const uint2* __restrict__ si_dst,
+                                             const uint2* __restrict__ si_src, uint2* __restrict__ p_out_same,
+                                             uint2* __restrict__ p_out_dst, uint2* __restrict__ p_in_same,
+                                             uint2* __restrict__ p_in_src) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t eo = aeid_out[i], ei = aeid_in[i];
         p_out_same[i] = so_src[eo];
@@ -165,25 +166,39 @@ __device__ __forceinline__ uint32_t first_later_from(const int64_t* __restrict__
     return first_later(t, a, b, x);
 }
 
+// Successor word for the first entry of a list [.., hi) at position p that is
+// later than time te: {p, gap to its time} (SUCC_END when p == hi).
+__device__ __forceinline__ uint2 succ_word(const int64_t* __restrict__ t, uint32_t p, uint32_t hi, int64_t te) {
+    if (p >= hi) return make_uint2(p, SUCC_END);
+    const uint64_t d = (uint64_t)(t[p] - te);
+    return make_uint2(p, d < SUCC_FAR ? (uint32_t)d : SUCC_FAR);
+}
+
 // Successor index: for every edge e = (u, v, t), the first position after t in
 // each of the four lists that touch it: out(u), in(v) (where e itself sits,
-// so the search starts just past e), out(v) and in(u).  A search level whose
-// candidate list belongs to an endpoint of the previous level's edge reads
-// its window start here instead of binary-searching the list.
+// so the search starts just past e), out(v) and in(u), with the time gap to
+// that entry.  A search level whose candidate list belongs to an endpoint of
+// the previous level's edge reads its window start here instead of
+// binary-searching the list, and skips the window when the gap already
+// exceeds it.
 __global__ void successor_kernel(int64_t m, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                  const int64_t* __restrict__ t, const uint32_t* __restrict__ off_out,
                                  const int64_t* __restrict__ at_out, const uint32_t* __restrict__ off_in,
                                  const int64_t* __restrict__ at_in, const uint32_t* __restrict__ pos_out,
-                                 const uint32_t* __restrict__ pos_in, uint32_t* __restrict__ so_src,
-                                 uint32_t* __restrict__ si_dst, uint32_t* __restrict__ so_dst,
-                                 uint32_t* __restrict__ si_src) {
+                                 const uint32_t* __restrict__ pos_in, uint2* __restrict__ so_src,
+                                 uint2* __restrict__ si_dst, uint2* __restrict__ so_dst,
+                                 uint2* __restrict__ si_src) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = src[e], v = dst[e];
         const int64_t te = t[e];
-        so_src[e] = first_later_from(at_out, pos_out[e] + 1, off_out[u + 1], te);
-        si_dst[e] = first_later_from(at_in, pos_in[e] + 1, off_in[v + 1], te);
-        so_dst[e] = first_later(at_out, off_out[v], off_out[v + 1], te);
-        si_src[e] = first_later(at_in, off_in[u], off_in[u + 1], te);
+        uint32_t hi = off_out[u + 1];
+        so_src[e] = succ_word(at_out, first_later_from(at_out, pos_out[e] + 1, hi, te), hi, te);
+        hi = off_in[v + 1];
+        si_dst[e] = succ_word(at_in, first_later_from(at_in, pos_in[e] + 1, hi, te), hi, te);
+        hi = off_out[v + 1];
+        so_dst[e] = succ_word(at_out, first_later(at_out, off_out[v], hi, te), hi, te);
+        hi = off_in[u + 1];
+        si_src[e] = succ_word(at_in, first_later(at_in, off_in[u], hi, te), hi, te);
     }
 }
 
@@ -392,7 +407,7 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
         v.pnbr = pn; v.pt = ptm; v.peid = pe;
     }
     // 6. successor index (window starts for lists that touch the previous edge)
-    uint32_t* nx[4];
+    uint2* nx[4];
     for (int j = 0; j < 4; ++j) TRY(owned(g, &nx[j], m));
     if (m > 0) {
         successor_kernel<<<grid_for(m, sms), 256, 0, st>>>(m, s_o, d_o, t_o, v.off[0], v.at[0], v.off[1], v.at[1],
@@ -402,7 +417,7 @@ tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
         TM_CUDA(cudaGetLastError());
     }
     for (int j = 0; j < 4; ++j) v.nxt[j] = nx[j];
-    uint32_t* px[4];
+    uint2* px[4];
     for (int j = 0; j < 4; ++j) TRY(owned(g, &px[j], m));
     if (m > 0) {
         successor_by_position_kernel<<<grid_for(m, sms), 256, 0, st>>>(

@@ -10,7 +10,10 @@
 //    window for edge i: the entries of one time-ordered adjacency list with
 //    t in (t_prev, min(t_root + delta, t_prev + gap_{i-1})], located by a
 //    binary search for the lower end and a galloping search for the upper end
-//    (the cached candidate range of Section 5.1.1 is the window itself).
+//    (the cached candidate range of Section 5.1.1 is the window itself).  When
+//    the list belongs to an endpoint of the edge just bound, the lower end is
+//    the graph's successor word for that edge instead, read together with the
+//    candidate; its time gap proves most windows empty without further loads.
 //  * The windows of a frame are flattened: lane j of a 32-wide step takes the
 //    j-th remaining candidate across all parents, so lanes stay busy even when
 //    every individual window is short.  Survivors of a step (structure, label
@@ -39,6 +42,8 @@ namespace tmg {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+// read the next level's successor words together with each candidate
+constexpr bool PREFETCH = true;
 constexpr uint32_t INLIST = 0x80000000u;    // window in an in-list
 constexpr uint32_t PAIRLIST = 0x40000000u;  // window in the (neighbour, time)-ordered out-list
 constexpr uint32_t POSMASK = 0x3FFFFFFFu;
@@ -231,12 +236,32 @@ struct Search {
     // 2 the edge list itself, 3 a pair-ordered list); prev_e is its edge id when
     // already loaded, else -1.  Successor-index lookups read the position-indexed
     // copy when it covers the continuation, else the edge-indexed one.
-    __device__ uint32_t successor(int nx, int cdir, uint32_t cpos, int32_t prev_e) const {
+    __device__ uint2 successor(int nx, int cdir, uint32_t cpos, int32_t prev_e) const {
         if (cdir == 0 && nx == NX_OUT_SRC) return __ldg(g.pnx[0] + cpos);
         if (cdir == 0 && nx == NX_OUT_DST) return __ldg(g.pnx[1] + cpos);
         if (cdir == 1 && nx == NX_IN_DST) return __ldg(g.pnx[2] + cpos);
         if (cdir == 1 && nx == NX_IN_SRC) return __ldg(g.pnx[3] + cpos);
         return __ldg(g.nxt[nx] + edge_at(cdir, cpos, prev_e));
+    }
+    // True when successor() is one load (no edge id needed first).
+    __device__ static bool successor_direct(int nx, int cdir) {
+        if (cdir == 2) return true;
+        if (cdir == 0) return nx == NX_OUT_SRC || nx == NX_OUT_DST;
+        if (cdir == 1) return nx == NX_IN_DST || nx == NX_IN_SRC;
+        return false;
+    }
+    // Successor words of the lists level `ln` draws its window from, after a
+    // candidate edge at position cpos of list cdir, read ahead together with
+    // the candidate: only those that take one load.  y == 0 means "not read".
+    __device__ void next_words(const LevelPlan& ln, int cdir, uint32_t cpos, uint2& wa, uint2& wb) const {
+        wa = make_uint2(0u, 0u);
+        wb = make_uint2(0u, 0u);
+        if (ln.nx_a >= 0 && successor_direct(ln.nx_a, cdir)) wa = successor(ln.nx_a, cdir, cpos, -1);
+        if (ln.kind == CLOSE && ln.nx_b >= 0 && successor_direct(ln.nx_b, cdir)) wb = successor(ln.nx_b, cdir, cpos, -1);
+    }
+    // True when a list whose successor word is w has no entry in (tprev, lim].
+    __device__ static bool word_shows_empty(uint2 w, uint64_t span) {
+        return w.y == SUCC_END || (uint64_t)w.y > span;
     }
     __device__ int32_t edge_at(int cdir, uint32_t cpos, int32_t prev_e) const {
         if (prev_e >= 0) return prev_e;
@@ -246,10 +271,17 @@ struct Search {
     }
 
     __device__ uint32_t locate(int lv_i, Frame pf, int ps, int nb, int32_t n0, int32_t n1, int32_t prev_e,
-                               int cdir, uint32_t cpos, int64_t tprev, int64_t tend, uint32_t& beg_out) {
+                               int cdir, uint32_t cpos, int64_t tprev, int64_t tend, uint32_t& beg_out,
+                               uint2 wa, uint2 wb) {
         const LevelPlan& lp = q->plan.lv[lv_i];
         auto slot = [&](int s) -> int32_t { return s < nb ? pf.node(s, ps) : (s == nb ? n0 : n1); };
         int64_t lim = min(tend, sat_add(tprev, lp.gap));
+        beg_out = 0;
+        if (!STATS && lim <= tprev) return 0;
+        const uint64_t span = (uint64_t)(lim - tprev);
+        // words read ahead: an empty list empties the window (a closing
+        // window is drawn from either of two lists)
+        if (!STATS && (word_shows_empty(wa, span) || word_shows_empty(wb, span))) return 0;
         const int64_t* tarr;
         uint32_t b, hi, flag = 0;
         int kind = lp.kind;
@@ -273,7 +305,15 @@ struct Search {
                     // edges straight from u's pair-ordered out-list instead of
                     // scanning the window for one neighbour
                     const int64_t* ta = g.at[dir];
-                    uint32_t b0 = nx >= 0 ? successor(nx, cdir, cpos, prev_e) : upper_bound_t(ta, lo, hi, tprev);
+                    uint32_t b0;
+                    if (nx >= 0) {
+                        const uint2 pw = dir ? wb : wa;
+                        const uint2 w = pw.y ? pw : successor(nx, cdir, cpos, prev_e);
+                        if (word_shows_empty(w, span)) return 0;
+                        b0 = w.x;
+                    } else {
+                        b0 = upper_bound_t(ta, lo, hi, tprev);
+                    }
                     uint32_t e0 = (b0 < hi) ? window_end(ta, b0, hi, lim) : b0;
                     if (e0 - b0 < PAIR_MIN_WINDOW) {
                         beg_out = b0 | (dir ? INLIST : 0u);
@@ -295,7 +335,14 @@ struct Search {
             }
             tarr = g.at[dir];
             flag = dir ? INLIST : 0u;
-            b = nx >= 0 ? successor(nx, cdir, cpos, prev_e) : upper_bound_t(tarr, lo, hi, tprev);
+            if (nx >= 0) {
+                const uint2 pw = (kind == CLOSE && dir) ? wb : wa;
+                const uint2 w = pw.y ? pw : successor(nx, cdir, cpos, prev_e);
+                if (!STATS && word_shows_empty(w, span)) return 0;
+                b = w.x;
+            } else {
+                b = upper_bound_t(tarr, lo, hi, tprev);
+            }
             if (STATS) acc.w[W_PROBE] += ceil_log2p1(hi - lo);
         }
         uint32_t e = (b < hi) ? window_end(tarr, b, hi, lim) : b;
@@ -403,10 +450,12 @@ struct Search {
         const bool need_eid = (MODE == MODE_FILL) || lp.elabel >= 0;
         int cdir = 2;
         uint32_t pos = 0;
+        uint2 wa = make_uint2(0u, 0u), wb = wa;   // next level's successor words, read with the candidate
         if (act) {
             uint32_t bw = f.beg(p);
             pos = (bw & POSMASK) + within;
             cdir = (bw & PAIRLIST) ? 3 : (kind == FREE ? 2 : ((bw & INLIST) ? 1 : 0));
+            if (PREFETCH && !STATS && i < k - 1) next_words(q->plan.lv[i + 1], cdir, pos, wa, wb);
             if (bw & PAIRLIST) {
                 // closing edge from the pair-ordered list: structure holds by construction
                 ct = __ldg(g.pt + pos);
@@ -451,7 +500,7 @@ struct Search {
         int64_t tend = 0;
         if (ok) {
             tend = f.tend(p);
-            clen = locate(i + 1, f, p, nb, n0, n1, ceid, cdir, pos, ct, tend, cbeg);
+            clen = locate(i + 1, f, p, nb, n0, n1, ceid, cdir, pos, ct, tend, cbeg, wa, wb);
         }
         if (STATS) {
             unsigned b = __ballot_sync(FULL, ok);
@@ -581,7 +630,9 @@ struct Search {
             bool ok = r < r1;
             int32_t s = 0, d = 0;
             int64_t tt = 0;
+            uint2 wa = make_uint2(0u, 0u), wb = wa;
             if (ok) {
+                if (PREFETCH && !STATS && k > 1) next_words(pl.lv[1], 2, (uint32_t)r, wa, wb);
                 s = __ldg(g.src + r);
                 d = __ldg(g.dst + r);
                 tt = __ldg(g.t + r);
@@ -601,7 +652,7 @@ struct Search {
             int64_t tend = 0;
             if (ok) {
                 tend = sat_add(tt, pl.delta);
-                clen = locate(1, Frame{wbase}, 0, 0, s, d, (int32_t)r, 2, (uint32_t)r, tt, tend, cbeg);
+                clen = locate(1, Frame{wbase}, 0, 0, s, d, (int32_t)r, 2, (uint32_t)r, tt, tend, cbeg, wa, wb);
             }
             if (STATS) {
                 unsigned b = __ballot_sync(FULL, ok);

@@ -52,18 +52,24 @@ struct GraphView {
     const int32_t* anbr[2];   // list entry neighbour (dst for out, src for in)
     const int32_t* aeid[2];   // list entry edge id
     // successor index, by edge id e = (u, v, t): first position with time > t in
-    // out(u), in(v), out(v), in(u) (absolute positions in the list columns)
-    const uint32_t* nxt[4];
+    // out(u), in(v), out(v), in(u).  Each word is {x: absolute position in the
+    // list columns, y: time of that entry minus t, saturated at SUCC_FAR, or
+    // SUCC_END when the list has no later entry}, so one load both starts a
+    // window and, for most windows, proves it empty.
+    const uint2* nxt[4];
     // the same, indexed by list position for the common continuations: [0] out-list
     // entry -> next later in that out-list, [1] out-list entry -> out(its neighbour),
     // [2] in-list entry -> next later in that in-list, [3] in-list entry -> in(its neighbour)
-    const uint32_t* pnx[4];
+    const uint2* pnx[4];
     // out-lists again, ordered by (neighbour, time) within each node (offsets off[0]):
     // the edges u -> v form one contiguous, time-ordered range
     const int32_t* pnbr;
     const int64_t* pt;
     const int32_t* peid;
 };
+
+constexpr uint32_t SUCC_END = 0xFFFFFFFFu;   // successor word: no later entry in the list
+constexpr uint32_t SUCC_FAR = 0xFFFFFFFEu;   // successor word: time gap >= this
 
 enum SuccKind : int8_t { NX_OUT_SRC = 0, NX_IN_DST = 1, NX_OUT_DST = 2, NX_IN_SRC = 3, NX_NONE = -1 };
 
