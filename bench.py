@@ -200,6 +200,31 @@ def run_reference(args, rank, ws):
 
 # --------------------------------------------------------------- GPU legs
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "search_count_traffic_powerlaw_10m.json")
+KERNEL_SOURCES = ("paper_2310_02800_gb300/csrc/search.cu", "paper_2310_02800_gb300/csrc/tm_internal.cuh",
+                  "paper_2310_02800_gb300/csrc/graph.cu")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload):
+    """DRAM bytes per count launch from the committed ncu capture of this kernel on this
+    workload; None when the kernel sources changed since it was taken."""
+    if workload != "powerlaw_10m" or not os.path.exists(TRAFFIC_FILE):
+        return None
+    d = json.load(open(TRAFFIC_FILE))
+    if d.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_count_launch"])
+
+
 def alg_bytes(w, k, matches_written, with_labels=False):
     """Algorithmic bytes of one search (see DESIGN: 17 B per root edge incl. label column
     when present, 32 B offset sector per located window, 16 B per window entry (+1 per window),
@@ -318,7 +343,9 @@ def main():
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "frac": achieved / pk["hbm_gbs"],
+                     "traffic": measured_traffic(args.workload) if args.scale == 1.0 else None,
+                     "alg_bytes_per_launch": int(b_low / len(queries)),
                      "kernel": "search_kernel<count>", "peak_source": pk["source"],
                      "with_notional_binary_search_GBps": b_full / (count_ms / 1000.0) / 1e9,
                      "alg_bytes_per_step": int(b_low),
