@@ -156,6 +156,29 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
         p.anti[a].xs = (int8_t)slot[m->anti_src[a]];
         p.anti[a].ys = (int8_t)slot[m->anti_dst[a]];
     }
+    // Look-ahead: a later motif edge j whose two nodes are both bound by
+    // edge i < j - 1 needs some graph edge between their images after t_i
+    // and within the root's delta; checking that when edge i binds prunes
+    // partial matches that cannot complete (the next edge is checked by its
+    // own window anyway).  Only for pairs no earlier motif edge joins: a
+    // chord between nodes that have not interacted yet rarely has an edge
+    // in the window, while a pair that recurs (ping-pongs) mostly does, and
+    // there the check costs more than it prunes.
+    for (int j = 2; j < k; ++j) {
+        const int x = m->esrc[j], y = m->edst[j];
+        const int bl = std::max(bound_at[x], bound_at[y]);
+        if (j < bl + 2) continue;
+        bool recurs = false;
+        for (int l = 0; l < j; ++l) recurs |= m->esrc[l] == x && m->edst[l] == y;
+        if (recurs) continue;
+        LevelPlan& L = p.lv[bl];
+        bool dup = false;
+        for (int l = 0; l < L.n_look; ++l) dup |= L.look_u[l] == slot[x] && L.look_v[l] == slot[y];
+        if (dup || L.n_look >= TM_MAX_LOOK) continue;
+        L.look_u[L.n_look] = (int8_t)slot[x];
+        L.look_v[L.n_look] = (int8_t)slot[y];
+        L.n_look++;
+    }
     p.warp_smem = std::max(16, (off_c + 15) & ~15);
     p.warp_smem_fill = std::max(16, (off_f + 15) & ~15);
     p.tune.warps_per_block = 4;
@@ -325,7 +348,7 @@ static tm_status run_count(tm_graph* g, tm_query* q, uint64_t rb, uint64_t re, c
     if (chunk_counts) TM_CUDA(cudaMemsetAsync(s.chunk_cnt, 0, (nch + 1) * 8, st));
     if (q->profile) TM_CUDA(cudaEventRecord(q->ev[0], st));
     r = launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block,
-                      q->plan.n_anti > 0, &s, st,
+                      plan_features(q->plan), &s, st,
                       grid_override, work);
     if (r != TM_OK) return r;
     if (q->profile) TM_CUDA(cudaEventRecord(q->ev[1], st));
@@ -498,7 +521,7 @@ extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_
         TM_CUDA(cudaMemcpyAsync(sc.head, sc.stage, sc.head_bytes(1), cudaMemcpyHostToDevice, st));
         if (q->profile) TM_CUDA(cudaEventRecord(q->ev[2], st));
         s = launch_search(g, MODE_FILL, sc.qdev(), 1, q->plan.warp_smem_fill, q->plan.tune.warps_per_block,
-                         q->plan.n_anti > 0, &sc, st);
+                         plan_features(q->plan), &sc, st);
         if (s != TM_OK) return s;
         if (q->profile) { TM_CUDA(cudaEventRecord(q->ev[3], st)); q->fill_timed = true; }
         TM_CUDA(cudaStreamSynchronize(st));
@@ -515,7 +538,7 @@ namespace tmg {
 // One captured CUDA graph per batch geometry: stage -> kernel -> read back.
 struct BatchExec {
     int nq = 0, warp_smem = 0, warps = 0;
-    bool anti = false;     // some query of the batch has anti-edges
+    unsigned feat = 0;     // union of the batch's plan features
     Scratch scratch;
     cudaGraphExec_t exec = nullptr;
     ~BatchExec() {
@@ -537,7 +560,7 @@ static tm_status capture_batch(tm_graph* g, BatchExec* b, cudaStream_t st) {
     cudaMemcpyAsync(s.head, s.stage, s.head_bytes(b->nq), cudaMemcpyHostToDevice, cs);
     cudaMemsetAsync(s.counters, 0, (size_t)b->nq * 8, cs);
     cudaMemsetAsync(s.ready, 0, s.task_cap, cs);
-    tm_status ls = launch_search(g, MODE_COUNT, s.qdev(), b->nq, b->warp_smem, b->warps, b->anti, &s, cs);
+    tm_status ls = launch_search(g, MODE_COUNT, s.qdev(), b->nq, b->warp_smem, b->warps, b->feat, &s, cs);
     cudaMemcpyAsync(s.counters_host, s.counters, (size_t)b->nq * 8, cudaMemcpyDeviceToHost, cs);
     cudaMemcpyAsync(s.stage, s.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, cs);
     e = cudaStreamEndCapture(cs, &graph);
@@ -564,26 +587,26 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
         return TM_OK;
     }
     int warp_smem = 16, warps = 0;
-    bool anti = false;
+    unsigned feat = 0;
     for (int j = 0; j < nq; ++j) {
         apply_cached_tuning(g, qs[j]);
         warp_smem = std::max(warp_smem, qs[j]->plan.warp_smem);
         warps = std::max(warps, qs[j]->plan.tune.warps_per_block);
-        anti |= qs[j]->plan.n_anti > 0;
+        feat |= plan_features(qs[j]->plan);
     }
     BatchExec* b = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_batch_mu);
         auto& vec = g_batches[g];
         for (auto& p : vec)
-            if (p->nq == nq && p->warp_smem == warp_smem && p->warps == warps && p->anti == anti) {
+            if (p->nq == nq && p->warp_smem == warp_smem && p->warps == warps && p->feat == feat) {
                 b = p.get();
                 break;
             }
         if (!b) {
             vec.emplace_back(new BatchExec());
             b = vec.back().get();
-            b->nq = nq; b->warp_smem = warp_smem; b->warps = warps; b->anti = anti;
+            b->nq = nq; b->warp_smem = warp_smem; b->warps = warps; b->feat = feat;
         }
     }
     tm_status s = scratch_reserve(&b->scratch, g->device, nq, (uint64_t)nq, 0, DEFAULT_TASK_CAP);

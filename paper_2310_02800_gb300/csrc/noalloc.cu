@@ -93,7 +93,7 @@ extern "C" tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, in
     const uint64_t m = (uint64_t)g->v.m;
     uint64_t chunk_base = 0;
     int warp_smem = 16, warps = 1;
-    bool anti = false;
+    unsigned feat = 0;
     for (int j = 0; j < nq; ++j) {
         if (!qs[j] || query_graph(qs[j]) != g) { set_error("null or mismatched query in batch"); return TM_E_INVALID; }
         QueryDev& qd = stage.q[j];
@@ -106,7 +106,7 @@ extern "C" tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, in
         qd.total = (unsigned long long*)totals_dev + j;
         warp_smem = std::max(warp_smem, qd.plan.warp_smem);
         warps = std::max(warps, qd.plan.tune.warps_per_block);
-        anti |= qd.plan.n_anti > 0;
+        feat |= plan_features(qd.plan);
     }
     stage.ctrl.total_chunks = chunk_base;
     // Every call reuses the array: rewrite the control block and the launch
@@ -123,7 +123,7 @@ extern "C" tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, in
     view.tasks = (Task*)(base + OFF_TASKS);
     view.ready = base + OFF_READY;
     view.task_cap = NOALLOC_TASKS;
-    s = launch_search(g, MODE_COUNT, (const QueryDev*)(base + OFF_QDEV), nq, warp_smem, warps, anti, &view, st);
+    s = launch_search(g, MODE_COUNT, (const QueryDev*)(base + OFF_QDEV), nq, warp_smem, warps, feat, &view, st);
     if (s != TM_OK) return s;
     unsigned int err = 0;
     TM_CUDA(cudaMemcpyAsync(&err, base + OFF_CTRL + offsetof(Ctrl, err), sizeof err, cudaMemcpyDeviceToHost, st));

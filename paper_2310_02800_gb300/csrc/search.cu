@@ -112,6 +112,27 @@ __device__ __forceinline__ uint32_t pair_count(const GraphView& g, int32_t u, in
     return b - a;
 }
 
+// Whether some edge u -> v has a time in (t0, t1]: u's pair-ordered out-list
+// holds the u -> v edges as one time-ordered run (binary search on the
+// neighbour, then a galloping search past t0 inside the run).
+__device__ __forceinline__ bool pair_after(const GraphView& g, int32_t u, int32_t v, int64_t t0, int64_t t1) {
+    if (t1 <= t0) return false;
+    const uint32_t u1 = __ldg(g.off[0] + u + 1);
+    uint32_t a = lower_bound_i32(g.pnbr, __ldg(g.off[0] + u), u1, v), hi = u1, step = 1;
+    while (true) {
+        const uint32_t probe = a + step - 1;
+        if (probe >= u1) break;                       // hi stays at the list end
+        if (__ldg(g.pnbr + probe) != v || __ldg(g.pt + probe) > t0) { hi = probe; break; }
+        a = probe + 1;
+        step <<= 1;
+    }
+    while (a < hi) {
+        const uint32_t mid = a + ((hi - a) >> 1);
+        if (__ldg(g.pnbr + mid) == v && __ldg(g.pt + mid) <= t0) a = mid + 1; else hi = mid;
+    }
+    return a < u1 && __ldg(g.pnbr + a) == v && __ldg(g.pt + a) <= t1;
+}
+
 // ------------------------------------------------------------ frame access
 
 struct Frame {
@@ -139,8 +160,10 @@ struct Acc {             // per-warp accumulators for the current query
     unsigned long long w[W_LEN];   // stats launches; lane-0 values except W_PROBE (per lane)
 };
 
-template <int MODE, bool STATS, bool ANTI>
+template <int MODE, bool STATS, int FEAT>
 struct Search {
+    static constexpr bool ANTI = (FEAT & FEAT_ANTI) != 0;   // anti-edge checks compiled in
+    static constexpr bool LOOK = (FEAT & FEAT_LOOK) != 0;   // look-ahead checks compiled in
     const GraphView& g;
     const QueryDev* __restrict__ qs;
     Ctrl* ctrl;
@@ -201,6 +224,18 @@ struct Search {
             uint32_t c = pair_count(g, slot(ap.xs), slot(ap.ys), ti, sat_add(ti, ap.delta));
             if (c > (uint32_t)ap.same_pair) return false;
         }
+        return true;
+    }
+
+    // Look-ahead of level `lp` for a partial match whose slots are the
+    // parent's [0, nb) plus n0, n1, just extended by an edge at time ct:
+    // false when a later motif edge between bound nodes has no graph edge left
+    // in (ct, tend].
+    __device__ bool look_ok(const LevelPlan& lp, Frame pf, int ps, int nb, int32_t n0, int32_t n1, int64_t ct,
+                            int64_t tend) const {
+        auto slot = [&](int s) -> int32_t { return s < nb ? pf.node(s, ps) : (s == nb ? n0 : n1); };
+        for (int l = 0; l < lp.n_look; ++l)
+            if (!pair_after(g, slot(lp.look_u[l]), slot(lp.look_v[l]), ct, tend)) return false;
         return true;
     }
 
@@ -488,6 +523,7 @@ struct Search {
             if (lp.elabel >= 0) ok &= g.elabel[ceid] == (uint8_t)lp.elabel;
             if (ANTI && ok && lp.anti_mask)
                 ok = anti_clear(lp.anti_mask, i, f, p, nb, n0, n1, ct, f.tprev(p), anti_off(i));
+            if (!STATS && LOOK && ok && lp.n_look) ok = look_ok(lp, f, p, nb, n0, n1, ct, f.tend(p));
         }
         uint32_t root = act ? f.root(p) : 0u;
         if (i == k - 1) {
@@ -642,6 +678,8 @@ struct Search {
                 if (pl.nl_y0 >= 0) ok &= g.nlabel[d] == (uint8_t)pl.nl_y0;
                 if (ANTI && ok && pl.anti_mask0)
                     ok = anti_clear(pl.anti_mask0, 0, Frame{wbase}, 0, 0, s, d, tt, tt, 0);
+                if (!STATS && LOOK && ok && pl.lv[0].n_look)
+                    ok = look_ok(pl.lv[0], Frame{wbase}, 0, 0, s, d, tt, sat_add(tt, pl.delta));
             }
             if (STATS && lane == 0) acc.w[W_ROOTS] += (r1 - rb < 32ull) ? (unsigned long long)(r1 - rb) : 32ull;
             if (k == 1) {
@@ -817,13 +855,13 @@ struct Search {
     }
 };
 
-template <int MODE, bool STATS, bool ANTI>
+template <int MODE, bool STATS, int FEAT>
 __global__ void __maxnreg__(56) search_kernel(const __grid_constant__ GraphView g,
                                                      const QueryDev* __restrict__ qs, int nq, int warp_smem,
                                                      Ctrl* ctrl, Task* tasks, uint8_t* ready, uint64_t task_cap) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5;
-    Search<MODE, STATS, ANTI> s(g, qs, ctrl, tasks, ready, task_cap, smem + (size_t)warp * warp_smem);
+    Search<MODE, STATS, FEAT> s(g, qs, ctrl, tasks, ready, task_cap, smem + (size_t)warp * warp_smem);
     s.run(nq, ctrl->total_chunks);
 }
 
@@ -833,14 +871,22 @@ namespace {
 std::mutex g_cfg_mu;
 std::unordered_map<uint64_t, int> g_blocks_per_sm;   // (device, kernel, warps, smem) -> resident blocks per SM
 
-// Kernel instances: count, count with anti-edges, count with work counters
-// (anti-edges included), fill, fill with anti-edges.  Motifs without
-// anti-edges run instances that hold none of their code.
-const void* kernel_of(Mode mode, bool stats, bool anti) {
-    if (mode == MODE_FILL)
-        return anti ? (const void*)search_kernel<MODE_FILL, false, true> : (const void*)search_kernel<MODE_FILL, false, false>;
-    if (stats) return (const void*)search_kernel<MODE_COUNT, true, true>;
-    return anti ? (const void*)search_kernel<MODE_COUNT, false, true> : (const void*)search_kernel<MODE_COUNT, false, false>;
+// Kernel instances: count and fill for each feature set (anti-edge checks,
+// look-ahead checks), and count with work counters (all features).  A query
+// runs the instance holding only the code its plan needs.
+template <int MODE>
+const void* kernel_for(unsigned feat) {
+    switch (feat & 3u) {
+        case 0: return (const void*)search_kernel<MODE, false, 0>;
+        case 1: return (const void*)search_kernel<MODE, false, 1>;
+        case 2: return (const void*)search_kernel<MODE, false, 2>;
+        default: return (const void*)search_kernel<MODE, false, 3>;
+    }
+}
+const void* kernel_of(Mode mode, bool stats, unsigned feat) {
+    if (mode == MODE_FILL) return kernel_for<MODE_FILL>(feat);
+    if (stats) return (const void*)search_kernel<MODE_COUNT, true, 3>;
+    return kernel_for<MODE_COUNT>(feat);
 }
 
 // Resident blocks per SM for one launch shape, computed once per shape.
@@ -865,20 +911,20 @@ LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int
     // keep the block's frames within the 227 KB of shared memory a block may use
     while (c.warps_per_block > 1 && max_warp_smem * c.warps_per_block > 232448) c.warps_per_block--;
     c.smem_bytes = max_warp_smem * c.warps_per_block;
-    int kid = mode == MODE_FILL ? 4 : 0;
-    c.grid = blocks_per_sm(g, kernel_of(mode, false, false), kid, c.warps_per_block * 32, c.smem_bytes) * g->num_sms;
+    int kid = mode == MODE_FILL ? 8 : 0;
+    c.grid = blocks_per_sm(g, kernel_of(mode, false, 0u), kid, c.warps_per_block * 32, c.smem_bytes) * g->num_sms;
     return c;
 }
 
 tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, int nq, int max_warp_smem,
-                        int warps_per_block, bool anti, const Scratch* s, cudaStream_t st, int grid_override,
+                        int warps_per_block, unsigned feat, const Scratch* s, cudaStream_t st, int grid_override,
                         bool stats) {
     LaunchCfg c = search_launch_cfg(g, mode, max_warp_smem, warps_per_block);
     int grid = grid_override > 0 ? grid_override : c.grid;
     if (mode == MODE_FILL) stats = false;
-    const void* fn = kernel_of(mode, stats, anti);
+    const void* fn = kernel_of(mode, stats, feat);
     // the instance's shared-memory limit (set once per launch shape)
-    blocks_per_sm(g, fn, (mode == MODE_FILL ? 4 : 0) + (stats ? 2 : 0) + (anti ? 1 : 0), c.warps_per_block * 32,
+    blocks_per_sm(g, fn, (mode == MODE_FILL ? 8 : 0) + (stats ? 4 : 0) + (int)(feat & 3u), c.warps_per_block * 32,
                   c.smem_bytes);
     GraphView v = g->v;
     Ctrl* ctrl = s->ctrl();

@@ -112,7 +112,7 @@ tm_status launch_batch(tm_server* s, Slot& sl) {
     memset(c, 0, sizeof(Ctrl));
     uint64_t base = 0;
     int warp_smem = 16, warps = 1;
-    bool anti = false, fanti = false;
+    unsigned feat = 0, ffeat = 0;
     for (int j = 0; j < nq; ++j) {
         Req* q = sl.batch[j];
         QueryDev* qd = cs.qdev_stage() + j;
@@ -127,8 +127,8 @@ tm_status launch_batch(tm_server* s, Slot& sl) {
         qd->chunk_cnt = q->enumerate ? q->chunk : nullptr;
         warp_smem = std::max(warp_smem, q->plan.warp_smem);
         warps = std::max(warps, q->plan.tune.warps_per_block);
-        anti |= q->plan.n_anti > 0;
-        if (q->enumerate) fanti |= q->plan.n_anti > 0;
+        feat |= plan_features(q->plan);
+        if (q->enumerate) ffeat |= plan_features(q->plan);
     }
     c->total_chunks = base;
     TM_CUDA(cudaMemcpyAsync(cs.head, cs.stage, cs.head_bytes(nq), cudaMemcpyHostToDevice, sl.st));
@@ -136,7 +136,7 @@ tm_status launch_batch(tm_server* s, Slot& sl) {
     TM_CUDA(cudaMemsetAsync(cs.ready, 0, cs.task_cap, sl.st));
     LaunchCfg lc = search_launch_cfg(g, MODE_COUNT, warp_smem, warps);
     int grid = std::max(1, std::min(lc.grid, s->grid_share * std::max(1, lc.grid / std::max(1, g->num_sms)) ));
-    r = launch_search(g, MODE_COUNT, cs.qdev(), nq, warp_smem, warps, anti, &cs, sl.st, grid);
+    r = launch_search(g, MODE_COUNT, cs.qdev(), nq, warp_smem, warps, feat, &cs, sl.st, grid);
     if (r != TM_OK) return r;
     // fill launch over the enumerate requests
     int ne = 0;
@@ -169,7 +169,7 @@ tm_status launch_batch(tm_server* s, Slot& sl) {
         TM_CUDA(cudaMemcpyAsync(fs.head, fs.stage, fs.head_bytes(ne), cudaMemcpyHostToDevice, sl.st));
         LaunchCfg lf = search_launch_cfg(g, MODE_FILL, fsmem, warps);
         int fgrid = std::max(1, std::min(lf.grid, s->grid_share * std::max(1, lf.grid / std::max(1, g->num_sms))));
-        r = launch_search(g, MODE_FILL, fs.qdev(), ne, fsmem, warps, fanti, &fs, sl.st, fgrid);
+        r = launch_search(g, MODE_FILL, fs.qdev(), ne, fsmem, warps, ffeat, &fs, sl.st, fgrid);
         if (r != TM_OK) return r;
     }
     TM_CUDA(cudaMemcpyAsync(cs.counters_host, cs.counters, (size_t)nq * 8, cudaMemcpyDeviceToHost, sl.st));

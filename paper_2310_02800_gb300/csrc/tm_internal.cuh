@@ -104,6 +104,8 @@ enum LevelKind : int8_t { EXT_OUT = 0, EXT_IN = 1, CLOSE = 2, FREE = 3 };
 // How one search level binds motif edge i (paper Section 5.1.2 "minfo"):
 // which mapped node supplies the candidate list, which mapped nodes a new
 // node must differ from, and the constraints checked on a candidate.
+constexpr int TM_MAX_LOOK = 3;
+
 struct LevelPlan {
     int8_t kind;       // LevelKind
     int8_t a;          // EXT_OUT: slot of x_i; EXT_IN: slot of y_i; CLOSE: slot of x_i
@@ -115,7 +117,10 @@ struct LevelPlan {
     int8_t nx_a;       // SuccKind giving the window start of the list used by EXT / CLOSE(out) levels
     int8_t nx_b;       // SuccKind for the in-list option of a CLOSE level
     uint8_t anti_mask; // anti-edges whose nodes and attached edge are all bound once edge i is
-    uint8_t pad1;
+    uint8_t n_look;    // later motif edges (after i+1) whose two nodes are first both bound by edge i
+    int8_t look_u[TM_MAX_LOOK];  // their endpoint slots: an edge look_u -> look_v must exist in
+    int8_t look_v[TM_MAX_LOOK];  // (t_i, t_root + delta], else no match extends this partial match
+    int8_t pad2[4];
     int32_t frame_off;       // byte offset of this level's frame in a warp's shared block (count)
     int32_t frame_off_fill;  // same, enumerate-fill layout (frames also carry edge ids)
     int32_t anti_row_off;    // byte offset of the anti-edge time rows within this level's frame
@@ -147,8 +152,17 @@ struct Plan {
     uint8_t anti_mask0;            // anti-edges checked when the root binds edge 0
     uint8_t pad1[3];
     AntiPlan anti[TM_MAX_ANTI];
-    LevelPlan lv[TM_MAX_EDGES];    // lv[i] for i = 1..k-1
+    LevelPlan lv[TM_MAX_EDGES];    // lv[i] for i = 1..k-1 (lv[0]: only the look-ahead of the root)
 };
+
+// Code a plan needs beyond plain search: anti-edge checks, look-ahead checks.
+constexpr unsigned FEAT_ANTI = 1u, FEAT_LOOK = 2u;
+inline unsigned plan_features(const Plan& p) {
+    unsigned f = p.n_anti > 0 ? FEAT_ANTI : 0u;
+    for (int i = 0; i < TM_MAX_EDGES; ++i)
+        if (p.lv[i].n_look) f |= FEAT_LOOK;
+    return f;
+}
 
 // Frame field offsets (bytes, relative to frame start), FCAP entries each.
 //   tprev i64, tend i64, beg u32 (bits 31/30: list kind), len u32, root u32,
@@ -263,10 +277,10 @@ struct LaunchCfg {
 
 // Launch the persistent search over nq queries (qdev already on the device).
 // Ctrl (incl. total_chunks) and qdev must already be initialised on the stream.
-// `anti` selects the kernel instance that checks anti-edges: it must be true
-// when any of the nq queries has one.
+// `feat` selects the kernel instance: the union of plan_features() over the
+// nq queries (an instance without a feature a query needs gives wrong counts).
 tm_status launch_search(const tm_graph* g, Mode mode, const QueryDev* qdev_dev, int nq,
-                        int max_warp_smem, int warps_per_block, bool anti,
+                        int max_warp_smem, int warps_per_block, unsigned feat,
                         const Scratch* s, cudaStream_t st, int grid_override = 0, bool stats = false);
 
 LaunchCfg search_launch_cfg(const tm_graph* g, Mode mode, int max_warp_smem, int warps_per_block);

@@ -89,6 +89,36 @@ def test_dense_uniform_many_motifs(tmg, seed):
             check_query(tmg, gg, og, synth.Motif(edges, delta, gaps, name=f"{edges} gaps"), enum_cap=1000)
 
 
+LOOKAHEAD_MOTIFS = [
+    [(0, 1), (1, 2), (0, 1), (1, 2)],
+    [(0, 1), (1, 2), (2, 0), (0, 1), (1, 2), (2, 0)],
+    [(0, 1), (1, 2), (2, 3), (0, 1), (3, 0)],
+    [(0, 1), (1, 2), (2, 0), (1, 0), (2, 1), (0, 2), (0, 1)],   # 4 later pairs bound at one level
+    [(0, 1), (1, 0), (0, 1), (1, 0), (0, 1), (1, 0), (0, 1)],
+    [(0, 1), (2, 3), (1, 2), (0, 3), (3, 0), (2, 1)],
+    [(0, 1), (2, 3), (1, 2), (0, 3), (3, 0), (2, 1), (1, 3), (3, 1)],   # more new pairs than are checked
+]
+
+
+@pytest.mark.parametrize("delta", [200, 600])
+def test_lookahead_motifs(tmg, delta):
+    """Motifs whose later edges join nodes bound early (the search prunes partial matches
+    whose later pairs have no edge left in the window): counts, per-root counts and rows,
+    with and without gaps, on an 8-node multigraph dense enough that most pairs recur."""
+    rng = np.random.default_rng(11)
+    n, m = 8, 4000
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    t = rng.integers(0, 20_000, m).astype(np.int64)
+    og = oracle.Graph(n, src, dst, t)
+    gg = tmg.Graph.load(n, src, dst, t)
+    for edges in LOOKAHEAD_MOTIFS:
+        k = len(edges)
+        check_query(tmg, gg, og, synth.Motif(edges, delta, name=str(edges)), enum_cap=5000)
+        gaps = [int(x) for x in rng.integers(30, delta, k - 1)]
+        check_query(tmg, gg, og, synth.Motif(edges, delta, gaps, name=f"{edges} gaps"), enum_cap=5000)
+
+
 def test_labels(tmg):
     rng = np.random.default_rng(5)
     n, m = 60, 8000
