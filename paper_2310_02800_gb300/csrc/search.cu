@@ -811,6 +811,8 @@ struct Search {
             if (MODE == MODE_FILL) {
                 out_base = q->chunk_off[lc];
                 out_local = 0;
+                // the count pass found no match rooted in this chunk: nothing to write
+                if (q->chunk_off[lc + 1] == out_base) continue;
                 if (out_base >= q->cap) {
                     // offsets never decrease: skip the rest of this query's chunks
                     unsigned long long nxt = (j + 1 < nq) ? qs[j + 1].chunk_base : total_chunks;

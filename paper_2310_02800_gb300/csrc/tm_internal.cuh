@@ -223,7 +223,7 @@ struct QueryDev {                    // one query of a launch
     unsigned long long* total;       // device counter
     unsigned long long* per_root;    // nullable (indexed by root - root_begin)
     unsigned long long* chunk_cnt;   // nullable (enumerate count pass)
-    const unsigned long long* chunk_off;  // enumerate fill: exclusive prefix of chunk_cnt
+    const unsigned long long* chunk_off;  // enumerate fill: exclusive prefix of chunk_cnt (n_chunks + 1 entries)
     int32_t* match_out;              // enumerate fill
     uint64_t cap;
     unsigned long long* work;        // nullable: tm_work counters (2 + 2*TM_MAX_EDGES + 1)
