@@ -116,10 +116,14 @@ typedef struct {
     int32_t split_min;
 } tm_tuning;
 
-/* Algorithm-independent work of one query: used as the numerator of the
- * bandwidth roofline.  nodes[i] = partial matches of i edges that locate a
- * window for edge i; entries[i] = candidates in those windows; probe_sectors
- * = sum over located windows of ceil(log2(list length + 1)). */
+/* Work of one query's search tree: used as the numerator of the bandwidth
+ * roofline.  nodes[i] = partial matches of i edges that locate a window for
+ * edge i; entries[i] = candidates in those windows; probe_sectors = sum over
+ * located windows of ceil(log2(list length + 1)).  For motifs without chords
+ * (no later edge between nodes that no earlier edge joins) this is the tree of
+ * the paper's Algorithm 1 (Section 2.2); otherwise the tree after the search's
+ * look-ahead pruning, which drops partial matches whose later chords have no
+ * graph edge left in the window. */
 typedef struct {
     uint64_t roots;
     uint64_t nodes[TM_MAX_EDGES];

@@ -523,7 +523,7 @@ struct Search {
             if (lp.elabel >= 0) ok &= g.elabel[ceid] == (uint8_t)lp.elabel;
             if (ANTI && ok && lp.anti_mask)
                 ok = anti_clear(lp.anti_mask, i, f, p, nb, n0, n1, ct, f.tprev(p), anti_off(i));
-            if (!STATS && LOOK && ok && lp.n_look) ok = look_ok(lp, f, p, nb, n0, n1, ct, f.tend(p));
+            if (LOOK && ok && lp.n_look) ok = look_ok(lp, f, p, nb, n0, n1, ct, f.tend(p));
         }
         uint32_t root = act ? f.root(p) : 0u;
         if (i == k - 1) {
@@ -678,7 +678,7 @@ struct Search {
                 if (pl.nl_y0 >= 0) ok &= g.nlabel[d] == (uint8_t)pl.nl_y0;
                 if (ANTI && ok && pl.anti_mask0)
                     ok = anti_clear(pl.anti_mask0, 0, Frame{wbase}, 0, 0, s, d, tt, tt, 0);
-                if (!STATS && LOOK && ok && pl.lv[0].n_look)
+                if (LOOK && ok && pl.lv[0].n_look)
                     ok = look_ok(pl.lv[0], Frame{wbase}, 0, 0, s, d, tt, sat_add(tt, pl.delta));
             }
             if (STATS && lane == 0) acc.w[W_ROOTS] += (r1 - rb < 32ull) ? (unsigned long long)(r1 - rb) : 32ull;
