@@ -183,6 +183,15 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
     p.warp_smem_fill = std::max(16, (off_f + 15) & ~15);
     p.tune.warps_per_block = 4;
     p.tune.chunk_roots = 64;
+    // stars of 5+ edges on a hub grow subtrees of C(window, k-1) matches:
+    // smaller root chunks spread the hubs' roots over more warps (the tuner
+    // picked 32 for every such shape on the power-law workload)
+    bool out_star = true, in_star = true;
+    for (int i = 1; i < k; ++i) {
+        out_star &= m->esrc[i] == m->esrc[0];
+        in_star &= m->edst[i] == m->edst[0];
+    }
+    if (k >= 5 && (out_star || in_star)) p.tune.chunk_roots = 32;
     p.tune.split_depth = k >= 3 ? 2 : (k == 2 ? 1 : 0);
     p.tune.split_min = 512;
     if (m->n_anti > 0) p.tune.split_depth = 0;   // donated tasks carry no anti-edge times
