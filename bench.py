@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip batched / served / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", default="powerlaw_10m",
-                    choices=["powerlaw_10m", "hubskew_100m", "serve_1b", "batch64"],
+                    choices=["powerlaw_10m", "hubskew_100m", "serve_1b", "batch64", "sweeps"],
                     help="powerlaw_10m: count + enumerate of 4 queries (default); hubskew_100m: count of the "
                          "labelled 5-edge path and the chorded 4-cycle; serve_1b: served Poisson traces on the "
-                         "1B-edge graph")
+                         "1B-edge graph; sweeps: constraint sweep (4-cycle N / V / V+T / V+T+A) and the "
+                         "ablation over delta on the 10M-edge graph")
     return ap.parse_args()
 
 
@@ -250,6 +251,8 @@ def main():
     stream = torch.cuda.Stream()
     if args.workload == "serve_1b":
         return serve_1b(args, dev)
+    if args.workload == "sweeps":
+        return sweeps(args, dev, stream)
     if args.workload == "batch64":
         import synth as _s
         g0 = _s.powerlaw_10m(scale=args.scale)
@@ -360,6 +363,42 @@ def main():
         line["cpu_baseline"] = cpu_leg(g, queries, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def sweeps(args, dev, stream, reps=3):
+    """Constraint sweep (the paper's Table 4 shape: a temporal 4-cycle with no constraints, node
+    labels, fine-grained gaps, an anti-edge) and the ablation against the paper's
+    thread-per-tree baseline over delta (the shape of its Fig. 9), on the 10M-edge graph
+    with two node labels."""
+    import torch
+    import synth
+    import paper_2310_02800_gb300 as tmg
+    g = synth.powerlaw_10m(scale=args.scale)
+    g.nlabel = synth.node_labels(g.n_nodes, 2, synth.SEED_BASE + 6)
+    out = {"workload": "sweeps", "config": {"graph": g.name, "node_labels": 2}}
+    with torch.cuda.stream(stream):
+        gg = tmg.Graph.from_synth(g, device=dev, stream=stream)
+        rows = []
+        for mo in synth.constraint_sweep_queries():
+            q = gg.compile(mo)
+            q.profile(True)
+            c = q.count(stream=stream)
+            ms = []
+            for _ in range(reps):
+                assert q.count(stream=stream) == c
+                ms.append(q.last_ms()[0])
+            rows.append({"query": mo.name, "matches": c, "count_ms": round(float(np.median(ms)), 4)})
+        out["constraints"] = rows
+        sweep = []
+        for delta in (900, 1800, 3600, 7200):
+            queries = synth.powerlaw_queries(delta)
+            qs = [gg.compile(q) for q in queries]
+            for q in qs:
+                q.profile(True)
+            for mo, r in ablation_leg(queries, qs, stream).items():
+                sweep.append(dict(delta_s=delta, query=mo, **r))
+        out["delta_sweep"] = sweep
+    print(json.dumps(out), flush=True)
 
 
 def ablation_leg(queries, qs, stream):

@@ -225,6 +225,20 @@ def powerlaw_queries(delta: int = 3600) -> list:
     return [cycle(3, delta), cycle(4, delta), out_star(3, delta), ping_pong(4, delta)]
 
 
+def constraint_sweep_queries(seed: int = SEED_BASE + 6, delta: int = 3600, n_labels: int = 2) -> list:
+    """Temporal 4-cycle under added constraints (a synthetic analogue of the paper's Table 4):
+    N none; V node labels on all four nodes (constants drawn from the seed); V+T also every
+    consecutive gap <= delta / 2; V+T+A also an anti-edge: no b -> a reply within delta / 4 of
+    the first edge a -> b."""
+    lab = [int(x % n_labels) for x in draws(seed, 401, 4)]
+    n = cycle(4, delta); n.name = "cycle4_N"
+    v = cycle(4, delta); v.nlabel = lab; v.name = "cycle4_V"
+    vt = cycle(4, delta); vt.nlabel = lab; vt.gaps = [delta // 2] * 3; vt.name = "cycle4_V+T"
+    vta = cycle(4, delta); vta.nlabel = lab; vta.gaps = [delta // 2] * 3
+    vta.anti = [(1, 0, 0, delta // 4)]; vta.name = "cycle4_V+T+A"
+    return [n, v, vt, vta]
+
+
 def hub_skewed_queries(seed: int = SEED_BASE + 3, delta: int = 7200) -> list:
     """5-edge temporal path with per-edge label constants and gaps <= 600 s; chorded 4-cycle."""
     d = draws(seed, 301, 5)

@@ -119,6 +119,18 @@ def test_lookahead_motifs(tmg, delta):
         check_query(tmg, gg, og, synth.Motif(edges, delta, gaps, name=f"{edges} gaps"), enum_cap=5000)
 
 
+def test_constraint_sweep_queries(tmg):
+    """The 4-cycle of the constraint sweep with no constraints, node labels, gaps and an
+    anti-edge, on a scaled power-law graph: counts and per-root counts equal the oracle's,
+    and each added constraint can only remove matches."""
+    g = _powerlaw_small(seed=77, n=4000, m=120_000)
+    g.nlabel = synth.node_labels(g.n_nodes, 2, 78)
+    og = oracle.Graph.from_synth(g)
+    gg = tmg.Graph.from_synth(g)
+    counts = [check_query(tmg, gg, og, mo, enum_cap=3000) for mo in synth.constraint_sweep_queries(delta=20_000)]
+    assert counts[0] >= counts[1] >= counts[2] >= counts[3] and counts[3] > 0, counts
+
+
 def test_labels(tmg):
     rng = np.random.default_rng(5)
     n, m = 60, 8000
@@ -230,6 +242,15 @@ def test_edge_cases(tmg):
     gg = tmg.Graph.load(8, src, dst, t)
     for delta in (70, 150, np.iinfo(np.int64).max):
         check_query(tmg, gg, og, synth.Motif(e8, int(delta)), enum_cap="all")
+    # time gaps beyond 32 bits (successor words saturate): windows decided by the full times
+    rng = np.random.default_rng(9)
+    src = rng.integers(0, 6, 300).astype(np.int32); dst = rng.integers(0, 6, 300).astype(np.int32)
+    t = np.sort(rng.integers(0, 40, 300)).astype(np.int64) * (2 ** 33) + rng.integers(0, 3, 300)
+    og = oracle.Graph(6, src, dst, t)
+    gg = tmg.Graph.load(6, src, dst, t)
+    for delta in (2 ** 32 - 3, 2 ** 32 + 5, 3 * 2 ** 33, 2 ** 40, np.iinfo(np.int64).max):
+        for mo in (synth.cycle(3, int(delta)), synth.ping_pong(4, int(delta)), synth.path(3, int(delta))):
+            check_query(tmg, gg, og, mo, enum_cap=2000)
     # invalid motifs are rejected with TM_E_INVALID
     with pytest.raises(tmg.TMError):
         gg.compile(synth.Motif([(0, 0)], 10))
