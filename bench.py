@@ -513,7 +513,7 @@ def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400, kmax=6):
         arr = synth.arrival_trace(rate, n, synth.SEED_BASE + 5, stream=700 + rate)
         reqs = [(float(arr[i]), i % len(qs), int(kinds[i % len(kinds)] % 10) < 3) for i in range(n)]
         configs = {}
-        for streams, max_batch in ((2, 16), (4, 4), (4, 1)):
+        for streams, max_batch in ((1, 16), (2, 16), (2, 4), (2, 1), (4, 4), (4, 1)):
             srv = gg.serve(mem_budget_bytes=8 << 30, streams=streams, max_batch=max_batch)
             lat, tickets = [], []
             t0 = time.perf_counter()
