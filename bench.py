@@ -498,7 +498,8 @@ def batched_leg(gg, dev, stream, dmax=3600.0, autotune=True):
     return out
 
 
-def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400, kmax=6):
+def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400, kmax=6,
+               shapes=((1, 16), (2, 16), (2, 4), (2, 1), (4, 4), (4, 1))):
     """Poisson arrivals (50 / 200 / 1000 q/s) of a 70% count / 30% enumerate mix (cap 1e6),
     k in 2..6, delta log-uniform in [60, dmax]: served (continuous batching) vs serial
     single-query execution of the same trace."""
@@ -513,7 +514,7 @@ def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400, kmax=6):
         arr = synth.arrival_trace(rate, n, synth.SEED_BASE + 5, stream=700 + rate)
         reqs = [(float(arr[i]), i % len(qs), int(kinds[i % len(kinds)] % 10) < 3) for i in range(n)]
         configs = {}
-        for streams, max_batch in ((1, 16), (2, 16), (2, 4), (2, 1), (4, 4), (4, 1)):
+        for streams, max_batch in shapes:
             srv = gg.serve(mem_budget_bytes=8 << 30, streams=streams, max_batch=max_batch)
             lat, tickets = [], []
             t0 = time.perf_counter()
@@ -575,7 +576,7 @@ def serve_1b(args, dev):
     del g
     # 2-4 edges, delta up to 10 minutes: longer windows on this graph's hubs make single
     # requests run for minutes, which a latency trace cannot absorb
-    res = served_leg(gg, dev, duration_s=2.0, dmax=600.0, max_requests=40, kmax=4)
+    res = served_leg(gg, dev, duration_s=2.0, dmax=600.0, max_requests=40, kmax=4, shapes=((2, 16), (4, 4)))
     line = {"metric": "p50/p99 latency and throughput, served vs serial", "workload": gg.n_edges,
             "config": {"workload": f"powerlaw_1b x{args.scale}", "n_edges": gg.n_edges, "n_nodes": gg.n_nodes,
                        "device_bytes": gg.device_bytes, "generate_s": gen_s, "load_s": load_s},

@@ -89,3 +89,31 @@ def test_poll_busy_then_done(setup):
     assert res is not None and res.total == og.count(synth.cycle(4, 3600))
     srv.release(tk)
     srv.stop()
+
+
+def test_mixed_feature_sets_in_one_launch(setup):
+    """Plain motifs, anti-edge motifs and motifs with look-ahead chords in one batched launch
+    and in one served mix (the launch runs the kernel instance with the union of their
+    features): every total equals the oracle's, and so do the enumerated rows."""
+    tmg, g, og, gg = setup
+    d = 20_000
+    mix = [synth.cycle(3, d), synth.path(3, d),
+           synth.Motif([(0, 1), (1, 2), (2, 0)], d, anti=[(1, 0, 0, d // 4)], name="cycle3_anti"),
+           synth.chorded_four_cycle(d),
+           synth.Motif([(0, 1), (1, 2), (2, 3), (0, 2)], d, name="path3_chord"),
+           synth.Motif([(0, 1), (1, 2), (2, 3), (0, 2)], d, anti=[(2, 1, 1, d // 2)], name="path3_chord_anti"),
+           synth.ping_pong(4, d)]
+    want = [og.count(q) for q in mix]
+    assert all(w > 0 for w in want[:2])
+    qs = [gg.compile(q) for q in mix]
+    assert gg.count_batch(qs) == want
+    assert gg.count_batch(qs[:2]) == want[:2]          # plain instance after the union one
+    srv = gg.serve(mem_budget_bytes=1 << 30, streams=2, max_batch=16)
+    tks = [srv.submit(q, enumerate=True, cap=want[i] + 3) for i, q in enumerate(qs)]
+    for i, tk in enumerate(tks):
+        r = srv.wait(tk)
+        assert r.total == want[i], mix[i].name
+        rows, _ = og.enumerate(mix[i], cap=want[i] + 3)
+        assert np.array_equal(rows_of(srv, r), rows), mix[i].name
+        srv.release(tk)
+    srv.stop()
