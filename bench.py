@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip batched / served / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", default="powerlaw_10m",
-                    choices=["powerlaw_10m", "hubskew_100m", "serve_1b", "batch64", "sweeps"],
+                    choices=["powerlaw_10m", "hubskew_100m", "serve_1b", "count_1b", "batch64", "sweeps"],
                     help="powerlaw_10m: count + enumerate of 4 queries (default); hubskew_100m: count of the "
                          "labelled 5-edge path and the chorded 4-cycle; serve_1b: served Poisson traces on the "
-                         "1B-edge graph; sweeps: constraint sweep (4-cycle N / V / V+T / V+T+A) and the "
+                         "1B-edge graph; count_1b: GPU ingest and counts of the four queries (delta 600 s) "
+                         "on the 1B-edge graph; sweeps: constraint sweep (4-cycle N / V / V+T / V+T+A) and the "
                          "ablation over delta on the 10M-edge graph")
     return ap.parse_args()
 
@@ -249,6 +250,8 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
+    if args.workload == "count_1b":
+        return count_1b(args, dev, stream)
     if args.workload == "serve_1b":
         return serve_1b(args, dev)
     if args.workload == "sweeps":
@@ -564,15 +567,58 @@ def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400, kmax=6,
     return out
 
 
-def serve_1b(args, dev):
-    """Served Poisson traces on the 1B-edge power-law graph (resident, ~53 GB)."""
+def powerlaw_1b_graph(scale):
+    """The 1B-edge, 100M-node graph: Zipf 2.1 popularity on both endpoints (no copy model:
+    at 1e9 edges preferential attachment puts ~15% of all edges on one node)."""
+    import synth
+    n = max(16, int(100_000_000 * scale)); m = max(16, int(1_000_000_000 * scale))
+    return synth.powerlaw_graph(n, m, synth.SEED_BASE + 5, alpha=2.1, span=94_608_000.0, pa=False)
+
+
+def count_1b(args, dev, stream, delta=600):
+    """GPU ingest of the 1B-edge graph from host arrays, then counts of the four power-law
+    queries (delta 600 s: longer windows on this graph's hubs make single counts run for
+    minutes)."""
+    import torch
     import synth
     import paper_2310_02800_gb300 as tmg
     t0 = time.perf_counter()
-    # Zipf 2.1 popularity on both endpoints (no copy model: at 1e9 edges preferential
-    # attachment puts ~15% of all edges on one node and single queries run for hours)
-    n = max(16, int(100_000_000 * args.scale)); m = max(16, int(1_000_000_000 * args.scale))
-    g = synth.powerlaw_graph(n, m, synth.SEED_BASE + 5, alpha=2.1, span=94_608_000.0, pa=False)
+    g = powerlaw_1b_graph(args.scale)
+    gen_s = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        gg = tmg.Graph.from_synth(g, device=dev, stream=stream)
+        torch.cuda.synchronize()
+        load_s = time.perf_counter() - t0
+        m = gg.n_edges
+        del g
+        queries = synth.powerlaw_queries(delta)
+        qs = [gg.compile(q) for q in queries]
+        rows = []
+        for mo, q in zip(queries, qs):
+            q.profile(True)
+            c = q.count(stream=stream)
+            ms = []
+            for _ in range(max(1, args.steps)):
+                assert q.count(stream=stream) == c
+                ms.append(q.last_ms()[0])
+            rows.append({"query": mo.name, "matches": c, "count_ms": round(float(np.median(ms)), 2),
+                         "root_edges_per_s": m / (float(np.median(ms)) / 1000.0)})
+    total_ms = sum(r["count_ms"] for r in rows)
+    print(json.dumps({"metric": "root-edges/s", "value": len(rows) * m / (total_ms / 1000.0), "unit": "root-edges/s",
+                      "workload": "count_1b",
+                      "config": {"graph": f"powerlaw_1b x{args.scale}", "n_edges": m, "n_nodes": gg.n_nodes,
+                                 "delta_s": delta, "device_bytes": gg.device_bytes, "generate_s": gen_s,
+                                 "upload_and_build_s": load_s},
+                      "queries": rows}), flush=True)
+
+
+def serve_1b(args, dev):
+    """Served Poisson traces on the resident 1B-edge power-law graph."""
+    import synth
+    import paper_2310_02800_gb300 as tmg
+    t0 = time.perf_counter()
+    g = powerlaw_1b_graph(args.scale)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     gg = tmg.Graph.from_synth(g, device=dev)
