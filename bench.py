@@ -228,9 +228,10 @@ def measured_traffic(workload):
 
 
 def alg_bytes(w, k, matches_written, with_labels=False):
-    """Algorithmic bytes of one search (see DESIGN: 17 B per root edge incl. label column
-    when present, 32 B offset sector per located window, 16 B per window entry (+1 per window),
-    32 B per binary-search probe sector, 4k B per written match row)."""
+    """Algorithmic bytes of one search: 16 B per root edge (17 with the label column), a
+    32 B offset sector per located window, 16 B per window entry plus one per window (the
+    read that ends it), 32 B per binary-search probe sector, 4k B per written match row.
+    Returns (with probe sectors, without)."""
     root_b = (17 if with_labels else 16) * w["roots"]
     nodes = sum(w["nodes"])
     entries = sum(w["entries"])
@@ -329,7 +330,7 @@ def main():
     b_full = sum(alg_bytes(w, q.k, 0, lab)[0] for w, q in zip(works, queries))
     b_low = sum(alg_bytes(w, q.k, 0, lab)[1] for w, q in zip(works, queries))
     # achieved counts the bytes of the search itself (root columns, one sector per located
-    # window, the window entries); the notional binary-search sectors of the survey's formula
+    # window, the window entries); the notional binary-search sectors of the full per-unit formula
     # are reported separately: with the successor index most windows need no search at all
     achieved = b_low / (count_ms / 1000.0) / 1e9
     launches_per_step = launches / args.steps
