@@ -47,6 +47,7 @@ constexpr bool PREFETCH = true;
 constexpr uint32_t INLIST = 0x80000000u;    // window in an in-list
 constexpr uint32_t PAIRLIST = 0x40000000u;  // window in the (neighbour, time)-ordered out-list
 constexpr uint32_t POSMASK = 0x3FFFFFFFu;
+constexpr uint32_t SPAN_FAR = 0xFFFFFFFFu;   // frame window end: recompute from the root
 constexpr uint32_t PAIR_MIN_DEG = 1024;     // closing lookups on shorter lists scan the time window
 constexpr uint32_t PAIR_MIN_WINDOW = 768;   // ... and so do windows shorter than this
 constexpr uint64_t WAIT_NS = 20ull * 1000 * 1000 * 1000;      // idle-wait deadline
@@ -138,7 +139,8 @@ __device__ __forceinline__ bool pair_after(const GraphView& g, int32_t u, int32_
 struct Frame {
     char* p;
     __device__ int64_t& tprev(int s) const { return ((int64_t*)(p + F_TPREV))[s]; }
-    __device__ int64_t& tend(int s) const { return ((int64_t*)(p + F_TEND))[s]; }
+    // window end t_root + delta, as its distance from tprev (SPAN_FAR: too far to hold)
+    __device__ uint32_t& tspan(int s) const { return ((uint32_t*)(p + F_TEND))[s]; }
     __device__ uint32_t& beg(int s) const { return ((uint32_t*)(p + F_BEG))[s]; }
     __device__ uint32_t& len(int s) const { return ((uint32_t*)(p + F_LEN))[s]; }
     __device__ uint32_t& root(int s) const { return ((uint32_t*)(p + F_ROOT))[s]; }
@@ -200,6 +202,17 @@ struct Search {
     __device__ void setP(int l, uint32_t v) { if (lane == l) myP = v; }
     __device__ void setOff(int l, uint32_t v) { if (lane == l) myOff = v; }
     __device__ void setT(int l, uint32_t v) { if (lane == l) myT = v; }
+
+    // The window end t_root + delta of entry s of frame f (4 bytes per entry
+    // instead of 8: rebuilt from the root edge's time when too far from tprev).
+    __device__ int64_t tend_of(Frame f, int s) const {
+        const uint32_t sp = f.tspan(s);
+        return sp != SPAN_FAR ? f.tprev(s) + (int64_t)sp : sat_add(__ldg(g.t + f.root(s)), q->plan.delta);
+    }
+    __device__ static void set_tend(Frame f, int s, int64_t tprev, int64_t tend) {
+        const uint64_t d = (uint64_t)(tend - tprev);   // tprev <= tend
+        f.tspan(s) = d < (uint64_t)SPAN_FAR ? (uint32_t)d : SPAN_FAR;
+    }
 
     __device__ Frame frame(int i) const {
         return Frame{wbase + (MODE == MODE_FILL ? q->plan.lv[i].frame_off_fill : q->plan.lv[i].frame_off)};
@@ -523,7 +536,7 @@ struct Search {
             if (lp.elabel >= 0) ok &= g.elabel[ceid] == (uint8_t)lp.elabel;
             if (ANTI && ok && lp.anti_mask)
                 ok = anti_clear(lp.anti_mask, i, f, p, nb, n0, n1, ct, f.tprev(p), anti_off(i));
-            if (LOOK && ok && lp.n_look) ok = look_ok(lp, f, p, nb, n0, n1, ct, f.tend(p));
+            if (LOOK && ok && lp.n_look) ok = look_ok(lp, f, p, nb, n0, n1, ct, tend_of(f, p));
         }
         uint32_t root = act ? f.root(p) : 0u;
         if (i == k - 1) {
@@ -535,7 +548,7 @@ struct Search {
         uint32_t cbeg = 0, clen = 0;
         int64_t tend = 0;
         if (ok) {
-            tend = f.tend(p);
+            tend = tend_of(f, p);
             clen = locate(i + 1, f, p, nb, n0, n1, ceid, cdir, pos, ct, tend, cbeg, wa, wb);
         }
         if (STATS) {
@@ -558,7 +571,7 @@ struct Search {
             if (nb_c > nb) c.node(nb, s) = n0;
             if (nb_c > nb + 1) c.node(nb + 1, s) = n1;
             c.tprev(s) = ct;
-            c.tend(s) = tend;
+            set_tend(c, s, ct, tend);
             c.beg(s) = cbeg;
             c.len(s) = clen;
             c.root(s) = root;
@@ -621,7 +634,7 @@ struct Search {
             t->beg = bw + skip;
             t->len = len - skip;
             t->tprev = f.tprev(p);
-            t->tend = f.tend(p);
+            t->tend = tend_of(f, p);
             t->root = f.root(p);
             for (int s = 0; s < nb; ++s) t->node[s] = f.node(s, p);
         }
@@ -711,7 +724,7 @@ struct Search {
                     c.node(0, sl) = s;
                     c.node(1, sl) = d;
                     c.tprev(sl) = tt;
-                    c.tend(sl) = tend;
+                    set_tend(c, sl, tt, tend);
                     c.beg(sl) = cbeg;
                     c.len(sl) = clen;
                     c.root(sl) = (uint32_t)r;
@@ -734,7 +747,7 @@ struct Search {
         Frame f = frame(i);
         if (lane == 0) {
             f.tprev(0) = tk.tprev;
-            f.tend(0) = tk.tend;
+            set_tend(f, 0, tk.tprev, tk.tend);
             f.beg(0) = tk.beg;
             f.len(0) = tk.len;
             f.root(0) = tk.root;

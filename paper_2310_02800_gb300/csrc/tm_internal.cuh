@@ -165,12 +165,13 @@ inline unsigned plan_features(const Plan& p) {
 }
 
 // Frame field offsets (bytes, relative to frame start), FCAP entries each.
-//   tprev i64, tend i64, beg u32 (bits 31/30: list kind), len u32, root u32,
+//   tprev i64, tend - tprev u32 (0xFFFFFFFF when it does not fit: t_root + delta is
+//   then rebuilt from the root edge), beg u32 (bits 31/30: list kind), len u32, root u32,
 //   node[nb] i32, eid[i] i32 (enumerate only), anti_t[n_anti] i64 (motifs with
 //   anti-edges: time of each anti-edge's attached edge once bound)
 constexpr int F_TPREV = 0;
 constexpr int F_TEND = F_TPREV + 8 * FCAP;
-constexpr int F_BEG = F_TEND + 8 * FCAP;
+constexpr int F_BEG = F_TEND + 4 * FCAP;
 constexpr int F_LEN = F_BEG + 4 * FCAP;
 constexpr int F_ROOT = F_LEN + 4 * FCAP;
 constexpr int F_NODE = F_ROOT + 4 * FCAP;
