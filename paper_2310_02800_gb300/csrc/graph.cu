@@ -78,9 +78,19 @@ __global__ void gather_edges_kernel(const uint32_t* __restrict__ perm, int64_t m
     }
 }
 
+// Degree histogram.  Lanes of a warp holding the same node add once for the
+// group: on power-law inputs a hub takes a large share of all endpoints, and
+// one atomic per edge on its counter serialises.  blockDim is a multiple of 32.
 __global__ void degree_kernel(const int32_t* __restrict__ node, int64_t m, unsigned long long* __restrict__ deg) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&deg[node[e]], 1ULL);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        const unsigned act = __ballot_sync(0xffffffffu, e < m);
+        if (e >= m) continue;
+        const int32_t v = node[e];
+        const unsigned grp = __match_any_sync(act, v);
+        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&deg[v], (unsigned long long)__popc(grp));
+    }
 }
 
 __global__ void node_keys_kernel(const int32_t* __restrict__ node, int64_t m, uint32_t* __restrict__ keys,
@@ -208,15 +218,17 @@ int bits_for(unsigned long long x) {
     return b;
 }
 
-struct Pool {  // temporary device allocations freed at scope exit
+struct Pool {  // temporary device allocations, stream-ordered, freed at scope exit
+    cudaStream_t st;
     std::vector<void*> ptrs;
+    explicit Pool(cudaStream_t s) : st(s) {}
     ~Pool() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) cudaFreeAsync(p, st);
     }
     template <typename T>
     tm_status get(T** out, size_t count) {
         void* p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 16)) != cudaSuccess) {
+        if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), st) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMalloc failed during graph build");
             return TM_E_OOM;
@@ -256,7 +268,7 @@ int grid_for(int64_t m, int sms) {
 tm_status build(tm_graph* g, const tm_edges* e, cudaStream_t st) {
     const int64_t m = e->n_edges, n = e->n_nodes;
     const int sms = g->num_sms;
-    Pool tmp;
+    Pool tmp(st);
     const int32_t *src = e->src, *dst = e->dst;
     const int64_t* t = e->t;
     const uint8_t* el = e->elabel;
@@ -456,6 +468,18 @@ extern "C" tm_status tm_graph_load(const tm_edges* e, int device, void* stream, 
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete g; return cuda_fail(cudaGetLastError(), "props"); }
     g->num_sms = prop.multiProcessorCount;
+    // keep up to 2 GiB of freed build temporaries in the device's stream-ordered
+    // pool, so loading graphs one after another does not go back to the driver
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = 0;
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (keep < (2ull << 30)) {
+            keep = 2ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
+    cudaGetLastError();
     tm_status s = build(g, e, (cudaStream_t)stream);
     if (s != TM_OK) {
         tm_graph_free(g);
