@@ -208,11 +208,17 @@ KERNEL_SOURCES = ("paper_2310_02800_gb300/csrc/search.cu", "paper_2310_02800_gb3
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources' code: line comments, surrounding blanks and empty
+    lines are left out, so an edit to comments alone keeps a capture valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*$", "", line).strip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

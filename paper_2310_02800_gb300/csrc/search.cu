@@ -29,6 +29,14 @@
 //    shallow level donates the upper half of its remaining candidate range to
 //    a device task queue (count mode only), and idle warps pop those tasks.
 //    Every device-side wait is bounded by a global-timer deadline.
+//  * Look-ahead on chords (our addition): when an edge binds the last node of
+//    a later motif edge whose node pair no earlier motif edge joins, some
+//    graph edge must join their images later in the root's window; the
+//    pair-ordered out-list answers that with two searches, and partial
+//    matches without one are dropped before their subtrees are searched.
+//  * The kernel is instantiated per mode (count, enumeration fill), with or
+//    without work counters, and per feature set (anti-edges, look-ahead), so
+//    a plain motif runs code holding neither.
 #include <cuda_runtime.h>
 
 #include <algorithm>
