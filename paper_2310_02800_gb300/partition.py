@@ -5,8 +5,12 @@ Edges are in time order (edge id = rank by (t, input index)).  A major
 partition is a contiguous range of root edges [root_begin, root_end).  Every
 match rooted there uses only edges with times in [t(root_begin),
 t(root_end - 1) + reach], where reach = delta plus the longest anti-edge
-window, so the partition's minor (halo) range [root_begin, edge_end) -- up to
-the last edge inside that time -- holds all it needs.  Each piece can be
+window, so the partition's minor (halo) range [edge_begin, edge_end) holds all
+it needs: it reaches forward to the last edge inside that time, and backward
+to the first edge whose time equals t(root_begin).  The backward part matters
+for anti-edges only: an anti-edge attached to motif edge 0 has the closed
+window [t(e_0), t(e_0) + delta'], which contains edges that tie with the root
+in time but precede it in id order, and those can sit before root_begin.  Each piece can be
 loaded, searched for its own roots and freed on its own: on one GPU this mines
 graphs larger than device memory piece by piece; across GPUs each piece is one
 GPU's work, with no exchange but the final sum.
@@ -25,6 +29,7 @@ class Piece:
     root_begin: int   # first root edge id (global)
     root_end: int     # one past the last root
     edge_end: int     # one past the last edge the piece's matches can use
+    edge_begin: int   # first edge the piece's matches can use: the first edge tied in time with root_begin
 
 
 def reach_of(motif) -> int:
@@ -46,7 +51,8 @@ def plan_pieces(t_sorted: np.ndarray, n_pieces: int, reach: int) -> list:
         last_t = int(t_sorted[b - 1])
         lim = last_t + reach if last_t <= np.iinfo(np.int64).max - reach else np.iinfo(np.int64).max
         e = int(np.searchsorted(t_sorted, lim, side="right"))
-        out.append(Piece(a, b, max(e, b)))
+        lo = int(np.searchsorted(t_sorted, int(t_sorted[a]), side="left"))
+        out.append(Piece(a, b, max(e, b), lo))
     return out
 
 
@@ -63,10 +69,11 @@ def count_by_pieces(n_nodes, src, dst, t, motif, n_pieces, elabel=None, nlabel=N
     s, d, tt, el = sort_edges(src, dst, t, elabel)
     total = 0
     for pc in plan_pieces(tt, n_pieces, reach_of(motif)):
-        sl = slice(pc.root_begin, pc.edge_end)
+        sl = slice(pc.edge_begin, pc.edge_end)
         g = Graph.load(n_nodes, s[sl], d[sl], tt[sl], None if el is None else el[sl], nlabel, device=device)
         q = g.compile(motif)
-        total += q.count_roots(0, pc.root_end - pc.root_begin)
+        # the slice keeps the global (t, id) order, so local id = global id - edge_begin
+        total += q.count_roots(pc.root_begin - pc.edge_begin, pc.root_end - pc.edge_begin)
         q.free()
         g.free()
     return total
