@@ -156,3 +156,83 @@ def star_burst(d):
 def star_burst_count(d, k):
     """Out-star with k leaves: any k of the d edges, in time order, has k distinct leaves."""
     return comb(d, k)
+
+
+# ------------------------------------------------------- search-tree work
+
+def _valid_prefix(combo, S, D, T, EL, edges, delta, gaps, elabel, nlabel, node_labels):
+    """phi of a prefix (e_0..e_{i-1}) of the motif's edges if it satisfies conditions 1-5
+    restricted to those edges, else None."""
+    ts = [T[e] for e in combo]
+    if any(ts[j] >= ts[j + 1] for j in range(len(ts) - 1)) or ts[-1] - ts[0] > delta:
+        return None
+    if any(ts[j + 1] - ts[j] > gaps[j] for j in range(len(ts) - 1)):
+        return None
+    phi = {}
+    for j, e in enumerate(combo):
+        x, y = edges[j]
+        for mn, gn in ((x, S[e]), (y, D[e])):
+            if phi.setdefault(mn, gn) != gn:
+                return None
+    if len(set(phi.values())) != len(phi):
+        return None
+    if elabel is not None and any(elabel[j] >= 0 and (EL is None or EL[e] != elabel[j]) for j, e in enumerate(combo)):
+        return None
+    if nlabel is not None and any(nlabel[mn] >= 0 and (node_labels is None or node_labels[gn] != nlabel[mn])
+                                  for mn, gn in phi.items()):
+        return None
+    return phi
+
+
+def search_work(src, dst, t, edges, delta, gaps=None, elabel=None, nlabel=None, edge_labels=None,
+                node_labels=None, roots=None):
+    """Work of Algorithm 1's search tree rooted at every edge, from its definition.
+
+    For each level i = 1..k-1: nodes[i] = the i-edge prefixes (e_0..e_{i-1}) that satisfy the
+    match conditions restricted to their own edges (each one locates a candidate list for
+    motif edge i); entries[i] = the summed number of list entries with time in
+    (t(e_{i-1}), min(t(e_0) + delta, t(e_{i-1}) + gap_{i-1})].  The list is out(phi(x_i)) when
+    only x_i is bound, in(phi(y_i)) when only y_i is, all edges when neither is, and when both
+    are, out(phi(x_i)) if its length is at most that of in(phi(y_i)), else in(phi(y_i)).
+    roots = (r0, r1) keeps only the trees whose root edge id lies in [r0, r1).
+    Returns (nodes, entries, list_lengths): list_lengths holds the length of every located list
+    (a binary search over a list of length L takes between floor(log2 L) and ceil(log2(L+1))
+    probes).
+    """
+    k = len(edges)
+    order = edge_order(t)
+    S = [int(src[i]) for i in order]
+    D = [int(dst[i]) for i in order]
+    T = [int(t[i]) for i in order]
+    EL = None if edge_labels is None else [int(edge_labels[i]) for i in order]
+    gaps = [BIG] * (k - 1) if gaps is None else [BIG if g is None else int(g) for g in gaps]
+    m = len(order)
+    out_l = {u: [e for e in range(m) if S[e] == u] for u in set(S)}
+    in_l = {v: [e for e in range(m) if D[e] == v] for v in set(D)}
+    nodes = [0] * 8
+    entries = [0] * 8
+    lengths = []
+    for i in range(1, k):
+        for combo in itertools.combinations(range(m), i):
+            if roots is not None and not roots[0] <= combo[0] < roots[1]:
+                continue
+            phi = _valid_prefix(combo, S, D, T, EL, edges[:i], delta, gaps, elabel, nlabel, node_labels)
+            if phi is None:
+                continue
+            nodes[i] += 1
+            x, y = edges[i]
+            u, v = phi.get(x), phi.get(y)
+            if u is not None and v is not None:
+                lst = out_l.get(u, []) if len(out_l.get(u, [])) <= len(in_l.get(v, [])) else in_l.get(v, [])
+            elif u is not None:
+                lst = out_l.get(u, [])
+            elif v is not None:
+                lst = in_l.get(v, [])
+            else:
+                lst = list(range(m))
+            tprev, t0 = T[combo[-1]], T[combo[0]]
+            lim = min(t0 + delta if t0 <= BIG - delta else BIG,
+                      tprev + gaps[i - 1] if tprev <= BIG - gaps[i - 1] else BIG)
+            entries[i] += sum(1 for e in lst if tprev < T[e] <= lim)
+            lengths.append(len(lst))
+    return nodes, entries, lengths

@@ -305,3 +305,39 @@ def test_anti_edge_monotone_and_vacuous():
     q = oracle.make_motif([(0, 1), (1, 2)], 3600, anti=[(0, 1, 0, 0)])
     p = oracle.make_motif([(0, 1), (1, 2)], 3600)
     assert og.count(q) <= og.count(p)
+
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_work_counters_brute_force(seed):
+    """The oracle's work counters (the roofline numerator) against the search tree computed
+    from its definition: per level, the valid prefixes and the entries of their candidate
+    windows; the binary-search probes within the bounds of a search over each located list."""
+    rng = np.random.default_rng(7000 + seed)
+    n_nodes = int(rng.integers(3, 7))
+    m = int(rng.integers(12, 22))
+    labels = 2 if seed % 2 else 0
+    src, dst, t, el, nl = rand_graph(rng, n_nodes, m, tmax=int(rng.integers(5, 40)), labels=labels)
+    og = oracle.Graph(n_nodes, src, dst, t, el, nl)
+    for edges in MOTIFS:
+        k = len(edges)
+        for delta in (2, 9, 1000):
+            gaps = [None if rng.random() < 0.6 else int(rng.integers(0, 12)) for _ in range(k - 1)]
+            elab = nlab = None
+            if labels:
+                elab = [-1] * k
+                elab[int(rng.integers(0, k))] = int(rng.integers(0, 2))
+                nlab = [-1] * 8
+                nlab[int(rng.integers(0, 1 + max(max(e) for e in edges)))] = int(rng.integers(0, 2))
+            q = oracle.make_motif(edges, delta, gaps, elab, nlab)
+            r0, r1 = (0, m) if delta != 9 else (m // 3, m - 2)
+            total, w = og.count(q, r0, r1, work=True)
+            nodes, entries, lengths = pins.search_work(src, dst, t, edges, delta, gaps, elab, nlab, el, nl,
+                                                       roots=(r0, r1))
+            assert w["roots"] == r1 - r0
+            assert w["nodes"] == nodes, (edges, delta, gaps)
+            assert w["entries"] == entries, (edges, delta, gaps)
+            lo = sum(int(np.floor(np.log2(L))) for L in lengths if L > 0)
+            hi = sum(int(np.ceil(np.log2(L + 1))) for L in lengths)
+            assert lo <= w["probes"] <= hi, (edges, delta, w["probes"], lo, hi)
+            assert w["matches"] == total
