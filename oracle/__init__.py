@@ -75,6 +75,8 @@ def _load():
         lib.or_count.argtypes = [p, ctypes.POINTER(Motif), ctypes.c_int64, ctypes.c_int64, p, p,
                                  ctypes.POINTER(Work)]
         lib.or_enumerate.argtypes = [p, ctypes.POINTER(Motif), p, ctypes.c_uint64, p, p]
+        lib.or_enumerate_roots.argtypes = [p, ctypes.POINTER(Motif), ctypes.c_int64, ctypes.c_int64, p,
+                                           ctypes.c_uint64, p, p]
         _lib = lib
     return _lib
 
@@ -160,15 +162,23 @@ class Graph:
             out.append(w.as_dict())
         return out[0] if len(out) == 1 else tuple(out)
 
-    def enumerate(self, motif, cap=None):
-        """(matches int32[n_written, k], total) -- lexicographically first cap matches."""
+    def enumerate(self, motif, cap=None, root_begin=None, root_end=None):
+        """(matches int32[n_written, k], total) -- lexicographically first cap matches, of the
+        whole graph or of the roots in [root_begin, root_end)."""
         q = motif if isinstance(motif, Motif) else motif_from(motif)
+        ranged = root_begin is not None or root_end is not None
+        r0 = 0 if root_begin is None else int(root_begin)
+        r1 = self.m if root_end is None else int(root_end)
         if cap is None:
-            cap = self.count(q)
+            cap = self.count(q, r0, r1)
         out = np.zeros((max(int(cap), 1), q.k), np.int32)
         nw = ctypes.c_uint64(0); tot = ctypes.c_uint64(0)
-        rc = _load().or_enumerate(self._h, ctypes.byref(q), out.ctypes.data, int(cap),
-                                  ctypes.addressof(nw), ctypes.addressof(tot))
+        if ranged:
+            rc = _load().or_enumerate_roots(self._h, ctypes.byref(q), r0, r1, out.ctypes.data, int(cap),
+                                            ctypes.addressof(nw), ctypes.addressof(tot))
+        else:
+            rc = _load().or_enumerate(self._h, ctypes.byref(q), out.ctypes.data, int(cap),
+                                      ctypes.addressof(nw), ctypes.addressof(tot))
         if rc != 0:
             raise ValueError("oracle: invalid motif")
         return out[: int(nw.value)], int(tot.value)

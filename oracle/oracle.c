@@ -324,3 +324,8 @@ int or_enumerate(const or_graph* g, const or_motif* q, int32_t* out, uint64_t ca
                  uint64_t* n_written, uint64_t* total) {
     return search(g, q, 0, g->m, total, NULL, out, cap, n_written, NULL);
 }
+
+int or_enumerate_roots(const or_graph* g, const or_motif* q, int64_t root_begin, int64_t root_end,
+                       int32_t* out, uint64_t cap, uint64_t* n_written, uint64_t* total) {
+    return search(g, q, root_begin, root_end, total, NULL, out, cap, n_written, NULL);
+}

@@ -49,4 +49,7 @@ int or_count(const or_graph* g, const or_motif* q, int64_t root_begin, int64_t r
 /* first min(cap, total) matches in lexicographic order, k int32 edge ids each */
 int or_enumerate(const or_graph* g, const or_motif* q, int32_t* out, uint64_t cap,
                  uint64_t* n_written, uint64_t* total);
+/* the same over the matches whose first edge id lies in [root_begin, root_end) */
+int or_enumerate_roots(const or_graph* g, const or_motif* q, int64_t root_begin, int64_t root_end,
+                       int32_t* out, uint64_t cap, uint64_t* n_written, uint64_t* total);
 #endif

@@ -146,11 +146,32 @@ def hub_skewed_100m(seed: int = SEED_BASE + 3, scale: float = 1.0) -> TemporalGr
 
 
 def powerlaw_1b(seed: int = SEED_BASE + 5, scale: float = 1.0) -> TemporalGraph:
-    """100M nodes, 1B edges, Zipf 2.1, same time process as powerlaw_10m."""
+    """100M nodes, 1B edges, Zipf 2.1 popularity on both endpoints, same time process as
+    powerlaw_10m.  No copy model for destinations: at 1e9 edges preferential attachment puts
+    about 15% of all edges on one node."""
     n = max(16, int(100_000_000 * scale)); m = max(16, int(1_000_000_000 * scale))
-    g = powerlaw_graph(n, m, seed, alpha=2.1, span=94_608_000.0)
+    g = powerlaw_graph(n, m, seed, alpha=2.1, span=94_608_000.0, pa=False)
     g.name = f"powerlaw_{n}n_{m}e"
     return g
+
+
+def time_windows(t: np.ndarray, n_windows: int, frac: float, seed: int, stream: int = 801) -> list:
+    """Seeded root samples of a graph given in input order: n_windows disjoint time windows
+    [T0, T1) that together hold about frac of all edges.  Because edge ids rank edges by
+    (t, input index), the edges of one window are one contiguous id range [a, b) with
+    a = #{t < T0} and b = #{t < T1}; returns (T0, T1, a, b) per window."""
+    m = int(t.shape[0])
+    tmin, tmax = int(t.min()), int(t.max()) + 1
+    per = max(1, int(m * frac / n_windows))
+    width = max(1, int((tmax - tmin) * per / m))
+    slots = max(1, (tmax - tmin) // width)
+    picks = sorted(set(int(x % slots) for x in draws(seed, stream, 4 * n_windows)))[:n_windows]
+    out = []
+    for p in picks:
+        t0 = tmin + p * width
+        t1 = t0 + width
+        out.append((t0, t1, int(np.count_nonzero(t < t0)), int(np.count_nonzero(t < t1))))
+    return out
 
 
 # ------------------------------------------------------------------ motifs

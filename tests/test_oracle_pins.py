@@ -223,6 +223,11 @@ def test_per_root_sum_and_ranges():
         cuts = [0, 5000, 5001, 12345, g.n_edges]
         assert sum(og.count(q, a, b) for a, b in zip(cuts[:-1], cuts[1:])) == tot
         assert np.array_equal(og.count(q, 5000, 12345, per_root=True)[1], pr[5000:12345])
+        # root-range enumeration: the shards' lists concatenate to the whole list
+        rows, _ = og.enumerate(q)
+        parts = [og.enumerate(q, root_begin=a, root_end=b)[0] for a, b in zip(cuts[:-1], cuts[1:])]
+        assert np.array_equal(np.concatenate(parts), rows)
+        assert all(np.all((p[:, 0] >= a) & (p[:, 0] < b)) for p, a, b in zip(parts, cuts[:-1], cuts[1:]))
 
 
 def test_enumeration_cap_and_order():
