@@ -211,6 +211,14 @@ tm_status tm_query_last_ms(const tm_query* q, double* search_ms, double* fill_ms
  * CUDA context stays usable).  kind 0 clears a pending fault. */
 tm_status tm_query_inject_fault(tm_query* q, int kind);
 
+/* Test hook for out-of-memory handling (failure injected on the host, no
+ * GPU fault): the device or pinned-host allocation that this library makes
+ * after `after` further successful ones fails as if the device were out of
+ * memory, and the call that made it returns TM_E_OOM with its outputs
+ * untouched (a served request completes with status TM_E_OOM).  Process-wide;
+ * one failure per arming; after < 0 disarms.  Every later call is unaffected. */
+tm_status tm_inject_alloc_failure(int64_t after);
+
 /* Number of CUDA kernels (and CUDA-graph replays) this library has launched
  * since it was loaded, over all threads. */
 uint64_t tm_kernel_launches(void);
@@ -234,7 +242,7 @@ tm_status tm_query_work(tm_graph* g, tm_query* q, void* stream, tm_work* out);
 
 /* Batched count that allocates nothing (the paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at query
- * time -- code inside a pre-planned CUDA-graph or real-time loop, processes
+ * time -- real-time loops that reserve all of their memory up front, processes
  * under a fixed memory cap or an allocator that forbids cudaMalloc after
  * start-up, plug-ins whose host framework owns every allocation).
  * Same result as tm_count_batch: the same persistent multi-query count kernel,
@@ -245,8 +253,11 @@ tm_status tm_query_work(tm_graph* g, tm_query* q, void* stream, tm_work* out);
  *   qs, nq     : compiled queries of graph g, 1 <= nq <= TM_NOALLOC_MAX_QUERIES
  *                (TM_E_INVALID beyond that, with a message naming the limit)
  *   totals_dev : device pointer uint64[nq], caller-owned; receives the counts
- * At most TM_NOALLOC_TASKS donated subtrees are queued at once (further
- * donations are kept by the donating warp; results are unchanged).
+ * The task queue has TM_NOALLOC_TASKS slots per call: slots are not reused
+ * within a call, so once a call has donated that many subtrees, further
+ * donations stay with the donating warp (results are unchanged).
+ * The launch records are staged in a static host buffer of about 60 KB (not on
+ * the caller's stack); the call's own stack use is under 1 KB.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  All calls share the one array, which keeps the
@@ -263,11 +274,23 @@ tm_status tm_count_batch_noalloc(tm_graph* g, tm_query* const* qs, int nq, void*
  * while their memory (match buffer + per-request scratch) fits the budget,
  * batched into persistent search launches on several streams, and completed
  * asynchronously.  Requests that arrive while others run are admitted as
- * streams and memory free up (continuous batching). */
+ * streams and memory free up (continuous batching).
+ *
+ * Batches are formed by expected cost: the graph keeps, per motif shape,
+ * delta bucket and flavour (count / enumerate), an estimate of the device time
+ * one request takes, learnt from the launches every server of the graph has
+ * timed.  The oldest admissible request leads each batch; a leader expected
+ * to take at least long_ms (or never seen) runs alone, and short requests
+ * behind it join while the batch's expected time stays within batch_ms.
+ * Short batches run on high-priority streams. */
 typedef struct {
     uint64_t mem_budget_bytes;   /* device bytes for match buffers + scratch (0 = 4 GiB) */
     int32_t streams;             /* concurrent batches in flight (0 = 2) */
     int32_t max_batch;           /* queries per launched batch (0 = 16) */
+    int32_t grid_pct;            /* share of the full persistent grid each launch uses, 1..100 (0 = 100) */
+    int32_t policy;              /* 0 = batches by expected cost (above); 1 = arrival order, any mix */
+    double long_ms;              /* expected device ms from which a request runs alone (0 = 1.0) */
+    double batch_ms;             /* expected device ms a batch of short requests may hold (0 = 2.0) */
 } tm_serve_cfg;
 
 typedef struct {
@@ -304,6 +327,17 @@ const char* tm_status_str(tm_status s);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* tm_last_error(void);
+
+/* Load-balancing diagnostics of the last count-mode search launch made by the
+ * calling thread (tm_count, tm_count_roots, tm_query_work, the count pass of
+ * tm_enumerate, tm_count_batch, tm_count_batch_noalloc).  Both pointers are
+ * host pointers and may be NULL.
+ *   donated  : subtrees handed to idle warps through the device task queue
+ *              (the sub-tree-level parallelism of Section 5.2)
+ *   reserved : task slots the launch's donors reserved; a value above the
+ *              queue's capacity means some donations found it full and their
+ *              work stayed with the donating warp */
+tm_status tm_last_search_stats(uint64_t* donated, uint64_t* reserved);
 
 #ifdef __cplusplus
 }

@@ -61,7 +61,9 @@ class _Work(ctypes.Structure):
 
 
 class _ServeCfg(ctypes.Structure):
-    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("grid_pct", ctypes.c_int32), ("policy", ctypes.c_int32), ("long_ms", ctypes.c_double),
+                ("batch_ms", ctypes.c_double)]
 
 
 class _Result(ctypes.Structure):
@@ -104,11 +106,25 @@ _SIGS = [
     ("tm_query_inject_fault", ctypes.c_int, [_P, ctypes.c_int]),
     ("tm_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tm_last_error", ctypes.c_char_p, []),
+    ("tm_last_search_stats", ctypes.c_int, [_U64P, _U64P]),
+    ("tm_inject_alloc_failure", ctypes.c_int, [ctypes.c_int64]),
 ]
 
 
 def kernel_launches() -> int:
     return int(lib().tm_kernel_launches())
+
+
+def last_search_stats() -> dict:
+    """Donation counters of the calling thread's last count-mode launch."""
+    d, r = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().tm_last_search_stats(ctypes.byref(d), ctypes.byref(r)))
+    return {"donated": int(d.value), "reserved": int(r.value)}
+
+
+def inject_alloc_failure(after: int = 0):
+    """Test hook: the library's allocation after `after` further successful ones fails (TM_E_OOM)."""
+    _check(lib().tm_inject_alloc_failure(int(after)))
 
 
 def library_path() -> str:
@@ -249,8 +265,11 @@ class Graph:
         _check(lib().tm_count_batch_noalloc(self._h, arr, len(queries), _stream_ptr(stream), _ptr(totals)))
         return totals
 
-    def serve(self, mem_budget_bytes=0, streams=0, max_batch=0) -> "Server":
-        cfg = _ServeCfg(int(mem_budget_bytes), int(streams), int(max_batch))
+    def serve(self, mem_budget_bytes=0, streams=0, max_batch=0, grid_pct=0, policy=0, long_ms=0.0,
+              batch_ms=0.0) -> "Server":
+        """Start a serving loop (tm_serve_start); zeros select the library defaults."""
+        cfg = _ServeCfg(int(mem_budget_bytes), int(streams), int(max_batch), int(grid_pct), int(policy),
+                        float(long_ms), float(batch_ms))
         h = ctypes.c_void_p()
         _check(lib().tm_serve_start(self._h, ctypes.byref(cfg), ctypes.byref(h)))
         return Server(self, h)

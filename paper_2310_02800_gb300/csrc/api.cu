@@ -16,11 +16,43 @@
 namespace tmg {
 
 static thread_local std::string g_last_error;
+static thread_local uint64_t g_last_donated = 0, g_last_reserved = 0;
 static std::atomic<uint64_t> g_launches{0};
 
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void note_search_stats(const Ctrl& c) {
+    g_last_donated = c.donated;
+    g_last_reserved = c.q_reserve;
+}
+
+// Allocations left before an injected failure (-1: none armed).
+static std::atomic<int64_t> g_alloc_fault{-1};
+
+static bool alloc_fault_due() {
+    int64_t v = g_alloc_fault.load();
+    while (v >= 0) {
+        if (g_alloc_fault.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (alloc_fault_due()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    if (alloc_fault_due()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t host_alloc_pinned(void** p, size_t bytes) {
+    if (alloc_fault_due()) return cudaErrorMemoryAllocation;
+    return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
 
 tm_status cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -203,7 +235,7 @@ tm_status build_plan(const tm_graph* g, const tm_motif* m, Plan* out) {
 // ------------------------------------------------------------- scratch
 
 static tm_status dev_alloc(void** p, size_t bytes) {
-    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    if (dev_malloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc failed for search scratch");
         return TM_E_OOM;
@@ -220,7 +252,7 @@ tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len,
         size_t bytes = s->head_bytes(nq);
         tm_status st = dev_alloc((void**)&s->head, bytes);
         if (st != TM_OK) return st;
-        if (cudaHostAlloc((void**)&s->stage, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        if (host_alloc_pinned((void**)&s->stage, bytes) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaHostAlloc failed");
             return TM_E_OOM;
@@ -234,7 +266,7 @@ tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len,
         s->counters = nullptr; s->counters_host = nullptr; s->counters_len = 0;
         tm_status st = dev_alloc((void**)&s->counters, counters_len * 8);
         if (st != TM_OK) return st;
-        if (cudaHostAlloc((void**)&s->counters_host, counters_len * 8, cudaHostAllocDefault) != cudaSuccess) {
+        if (host_alloc_pinned((void**)&s->counters_host, counters_len * 8) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaHostAlloc failed");
             return TM_E_OOM;
@@ -369,6 +401,7 @@ static tm_status read_back(Scratch& s, cudaStream_t st, uint64_t n_counters) {
     TM_CUDA(cudaMemcpyAsync(s.counters_host, s.counters, n_counters * 8, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaMemcpyAsync(s.stage, s.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
+    note_search_stats(*s.ctrl_stage());
     if (s.ctrl_stage()->err) {
         set_error("a bounded device wait timed out");
         return TM_E_TIMEOUT;
@@ -544,34 +577,119 @@ extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_
 
 namespace tmg {
 
-// One captured CUDA graph per batch geometry: stage -> kernel -> read back.
+std::vector<LaunchGroup> occupancy_groups(const tm_graph* g, Mode mode, const Plan* const* plans, int nq,
+                                          int* order) {
+    std::vector<int> grid(nq), wpb(nq);
+    for (int j = 0; j < nq; ++j) {
+        const Plan& p = *plans[j];
+        LaunchCfg c = search_launch_cfg(g, mode, mode == MODE_FILL ? p.warp_smem_fill : p.warp_smem,
+                                        p.tune.warps_per_block);
+        grid[j] = c.grid;
+        wpb[j] = c.warps_per_block;
+        order[j] = j;
+    }
+    // highest occupancy first; arrival order within a group
+    std::stable_sort(order, order + nq, [&](int a, int b) {
+        return grid[a] != grid[b] ? grid[a] > grid[b] : wpb[a] > wpb[b];
+    });
+    std::vector<LaunchGroup> out;
+    for (int i = 0; i < nq; ++i) {
+        const int j = order[i];
+        const Plan& p = *plans[j];
+        if (out.empty() || grid[order[out.back().first]] != grid[j] || wpb[order[out.back().first]] != wpb[j])
+            out.push_back(LaunchGroup{i, 0, 16, wpb[j], 0u});
+        LaunchGroup& lg = out.back();
+        lg.count++;
+        lg.warp_smem = std::max(lg.warp_smem, mode == MODE_FILL ? p.warp_smem_fill : p.warp_smem);
+        lg.feat |= plan_features(p);
+    }
+    return out;
+}
+
+// One captured CUDA graph per batch geometry (its occupancy groups): stage ->
+// one persistent launch per group, back to back -> read back.  Device and
+// pinned staging: a control block per group, then the launch records in group
+// order.
 struct BatchExec {
-    int nq = 0, warp_smem = 0, warps = 0;
-    unsigned feat = 0;     // union of the batch's plan features
-    Scratch scratch;
+    int nq = 0;
+    std::vector<LaunchGroup> groups;
+    char* head = nullptr;                      // device: Ctrl[groups] + QueryDev[nq]
+    char* stage = nullptr;                     // pinned mirror
+    unsigned long long* counters = nullptr;    // device totals, by the caller's query index
+    unsigned long long* counters_host = nullptr;
+    Task* tasks = nullptr;
+    uint8_t* ready = nullptr;
     cudaGraphExec_t exec = nullptr;
-    ~BatchExec() {
+    std::mutex mu;                             // one call at a time uses these buffers
+    size_t ctrl_bytes() const { return groups.size() * sizeof(Ctrl); }
+    size_t head_bytes() const { return ctrl_bytes() + (size_t)nq * sizeof(QueryDev); }
+    QueryDev* qdev_stage() const { return (QueryDev*)(stage + ctrl_bytes()); }
+    QueryDev* qdev_dev() const { return (QueryDev*)(head + ctrl_bytes()); }
+    bool same_shape(int n, const std::vector<LaunchGroup>& gs) const {
+        if (n != nq || gs.size() != groups.size()) return false;
+        for (size_t i = 0; i < gs.size(); ++i)
+            if (gs[i].count != groups[i].count || gs[i].warp_smem != groups[i].warp_smem ||
+                gs[i].warps != groups[i].warps || gs[i].feat != groups[i].feat)
+                return false;
+        return true;
+    }
+    tm_status alloc() {
+        if (head) return TM_OK;
+        tm_status s = dev_alloc((void**)&head, head_bytes());
+        if (s == TM_OK) s = dev_alloc((void**)&counters, (size_t)nq * 8);
+        if (s == TM_OK) s = dev_alloc((void**)&tasks, DEFAULT_TASK_CAP * sizeof(Task));
+        if (s == TM_OK) s = dev_alloc((void**)&ready, DEFAULT_TASK_CAP);
+        if (s == TM_OK && (host_alloc_pinned((void**)&stage, head_bytes()) != cudaSuccess ||
+                           host_alloc_pinned((void**)&counters_host, (size_t)nq * 8) != cudaSuccess)) {
+            cudaGetLastError();
+            set_error("cudaHostAlloc failed");
+            s = TM_E_OOM;
+        }
+        if (s != TM_OK) release();
+        return s;
+    }
+    void release() {
         if (exec) cudaGraphExecDestroy(exec);
-        scratch_free(&scratch);
+        if (head) cudaFree(head);
+        if (counters) cudaFree(counters);
+        if (tasks) cudaFree(tasks);
+        if (ready) cudaFree(ready);
+        if (stage) cudaFreeHost(stage);
+        if (counters_host) cudaFreeHost(counters_host);
+        exec = nullptr; head = stage = nullptr; counters = counters_host = nullptr; tasks = nullptr; ready = nullptr;
+    }
+    ~BatchExec() { release(); }
+    Scratch view(size_t gi) const {   // what one group's launch reads: its Ctrl and the task queue
+        Scratch v;
+        v.head = head + gi * sizeof(Ctrl);
+        v.tasks = tasks;
+        v.ready = ready;
+        v.task_cap = DEFAULT_TASK_CAP;
+        return v;
     }
 };
 
 static std::mutex g_batch_mu;
 static std::map<const tm_graph*, std::vector<std::unique_ptr<BatchExec>>> g_batches;
 
-static tm_status capture_batch(tm_graph* g, BatchExec* b, cudaStream_t st) {
-    Scratch& s = b->scratch;
+static tm_status capture_batch(tm_graph* g, BatchExec* b) {
     cudaStream_t cs;
     TM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "begin capture"); }
-    cudaMemcpyAsync(s.head, s.stage, s.head_bytes(b->nq), cudaMemcpyHostToDevice, cs);
-    cudaMemsetAsync(s.counters, 0, (size_t)b->nq * 8, cs);
-    cudaMemsetAsync(s.ready, 0, s.task_cap, cs);
-    tm_status ls = launch_search(g, MODE_COUNT, s.qdev(), b->nq, b->warp_smem, b->warps, b->feat, &s, cs);
-    cudaMemcpyAsync(s.counters_host, s.counters, (size_t)b->nq * 8, cudaMemcpyDeviceToHost, cs);
-    cudaMemcpyAsync(s.stage, s.head, sizeof(Ctrl), cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(b->head, b->stage, b->head_bytes(), cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(b->counters, 0, (size_t)b->nq * 8, cs);
+    tm_status ls = TM_OK;
+    for (size_t gi = 0; gi < b->groups.size() && ls == TM_OK; ++gi) {
+        const LaunchGroup& lg = b->groups[gi];
+        Scratch v = b->view(gi);
+        cudaMemsetAsync(b->ready, 0, DEFAULT_TASK_CAP, cs);
+        ls = launch_search(g, MODE_COUNT, b->qdev_dev() + lg.first, lg.count, lg.warp_smem, lg.warps, lg.feat, &v,
+                           cs);
+    }
+    cudaMemcpyAsync(b->counters_host, b->counters, (size_t)b->nq * 8, cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(b->stage, b->head, b->ctrl_bytes(), cudaMemcpyDeviceToHost, cs);
     e = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (ls != TM_OK) { if (graph) cudaGraphDestroy(graph); return ls; }
@@ -579,7 +697,6 @@ static tm_status capture_batch(tm_graph* g, BatchExec* b, cudaStream_t st) {
     e = cudaGraphInstantiate(&b->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-    (void)st;
     return TM_OK;
 }
 
@@ -595,56 +712,67 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
         for (int j = 0; j < nq; ++j) totals[j] = 0;
         return TM_OK;
     }
-    int warp_smem = 16, warps = 0;
-    unsigned feat = 0;
+    std::vector<const Plan*> plans(nq);
     for (int j = 0; j < nq; ++j) {
         apply_cached_tuning(g, qs[j]);
-        warp_smem = std::max(warp_smem, qs[j]->plan.warp_smem);
-        warps = std::max(warps, qs[j]->plan.tune.warps_per_block);
-        feat |= plan_features(qs[j]->plan);
+        plans[j] = &qs[j]->plan;
     }
+    std::vector<int> order(nq);
+    std::vector<LaunchGroup> groups = occupancy_groups(g, MODE_COUNT, plans.data(), nq, order.data());
     BatchExec* b = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_batch_mu);
         auto& vec = g_batches[g];
         for (auto& p : vec)
-            if (p->nq == nq && p->warp_smem == warp_smem && p->warps == warps && p->feat == feat) {
+            if (p->same_shape(nq, groups)) {
                 b = p.get();
                 break;
             }
         if (!b) {
             vec.emplace_back(new BatchExec());
             b = vec.back().get();
-            b->nq = nq; b->warp_smem = warp_smem; b->warps = warps; b->feat = feat;
+            b->nq = nq;
+            b->groups = groups;
         }
     }
-    tm_status s = scratch_reserve(&b->scratch, g->device, nq, (uint64_t)nq, 0, DEFAULT_TASK_CAP);
+    std::lock_guard<std::mutex> use(b->mu);
+    tm_status s = b->alloc();
     if (s != TM_OK) return s;
-    Scratch& sc = b->scratch;
-    Ctrl* c = sc.ctrl_stage();
-    memset(c, 0, sizeof(Ctrl));
-    uint64_t base = 0;
-    for (int j = 0; j < nq; ++j) {
-        QueryDev* qd = sc.qdev_stage() + j;
-        memset(qd, 0, sizeof(QueryDev));
-        qd->plan = qs[j]->plan;
-        qd->root_begin = 0;
-        qd->root_end = (uint64_t)g->v.m;
-        qd->n_chunks = n_chunks((uint64_t)g->v.m, qs[j]->plan.tune.chunk_roots);
-        qd->chunk_base = base;
-        base += qd->n_chunks;
-        qd->total = sc.counters + j;
+    memset(b->stage, 0, b->ctrl_bytes());
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        uint64_t base = 0;
+        for (int i = groups[gi].first; i < groups[gi].first + groups[gi].count; ++i) {
+            const int j = order[i];
+            QueryDev* qd = b->qdev_stage() + i;
+            memset(qd, 0, sizeof(QueryDev));
+            qd->plan = qs[j]->plan;
+            qd->root_begin = 0;
+            qd->root_end = (uint64_t)g->v.m;
+            qd->n_chunks = n_chunks((uint64_t)g->v.m, qs[j]->plan.tune.chunk_roots);
+            qd->chunk_base = base;
+            base += qd->n_chunks;
+            qd->total = b->counters + j;
+        }
+        ((Ctrl*)b->stage)[gi].total_chunks = base;
     }
-    c->total_chunks = base;
     if (!b->exec) {
-        s = capture_batch(g, b, st);
+        s = capture_batch(g, b);
         if (s != TM_OK) return s;
     }
     TM_CUDA(cudaGraphLaunch(b->exec, st));
     note_launches(1);
     TM_CUDA(cudaStreamSynchronize(st));
-    if (sc.ctrl_stage()->err) { set_error("a bounded device wait timed out"); return TM_E_TIMEOUT; }
-    for (int j = 0; j < nq; ++j) totals[j] = sc.counters_host[j];
+    Ctrl sum;
+    memset(&sum, 0, sizeof sum);
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const Ctrl& c = ((const Ctrl*)b->stage)[gi];
+        sum.donated += c.donated;
+        sum.q_reserve += c.q_reserve;
+        sum.err |= c.err;
+    }
+    note_search_stats(sum);
+    if (sum.err) { set_error("a bounded device wait timed out"); return TM_E_TIMEOUT; }
+    for (int j = 0; j < nq; ++j) totals[j] = b->counters_host[j];
     return TM_OK;
 }
 
@@ -739,5 +867,16 @@ extern "C" const char* tm_status_str(tm_status s) {
 }
 
 extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" tm_status tm_inject_alloc_failure(int64_t after) {
+    g_alloc_fault.store(after < 0 ? -1 : after);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_last_search_stats(uint64_t* donated, uint64_t* reserved) {
+    if (donated) *donated = g_last_donated;
+    if (reserved) *reserved = g_last_reserved;
+    return TM_OK;
+}
 
 extern "C" uint64_t tm_kernel_launches(void) { return g_launches.load(); }

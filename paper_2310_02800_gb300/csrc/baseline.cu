@@ -153,7 +153,7 @@ extern "C" tm_status tm_count_baseline(tm_graph* g, tm_query* q, void* stream, u
     for (int i = 0; i < TM_MAX_EDGES - 1; ++i) bm.gap[i] = m->gap[i];
     for (int j = 0; j < TM_MAX_NODES; ++j) bm.nlabel[j] = m->nlabel[j];
     unsigned long long* d_total = nullptr;
-    TM_CUDA(cudaMallocAsync((void**)&d_total, sizeof(unsigned long long), st));
+    TM_CUDA(dev_malloc_async((void**)&d_total, sizeof(unsigned long long), st));
     TM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), st));
     cudaEvent_t e0, e1;
     TM_CUDA(cudaEventCreate(&e0));

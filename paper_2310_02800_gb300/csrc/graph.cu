@@ -228,7 +228,7 @@ struct Pool {  // temporary device allocations, stream-ordered, freed at scope e
     template <typename T>
     tm_status get(T** out, size_t count) {
         void* p = nullptr;
-        if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), st) != cudaSuccess) {
+        if (dev_malloc_async(&p, std::max<size_t>(count * sizeof(T), 16), st) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMalloc failed during graph build");
             return TM_E_OOM;
@@ -243,7 +243,7 @@ template <typename T>
 tm_status owned(tm_graph* g, T** out, size_t count) {
     void* p = nullptr;
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dev_malloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc failed for graph storage");
         return TM_E_OOM;

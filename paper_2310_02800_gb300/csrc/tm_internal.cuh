@@ -20,6 +20,13 @@ void set_error(const std::string& msg);
 void note_launches(uint64_t n);
 tm_status cuda_fail(cudaError_t e, const char* what);
 
+// Every device and pinned-host allocation of the library goes through these,
+// so that tm_inject_alloc_failure can make one of them fail like an
+// out-of-memory device (cudaErrorMemoryAllocation, nothing allocated).
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st);
+cudaError_t host_alloc_pinned(void** p, size_t bytes);
+
 // Select the device and drop any error another library left on this thread,
 // so that only this call's own CUDA errors are reported.
 #define TM_ENTER(dev)                                         \
@@ -93,6 +100,10 @@ struct tm_graph {
     int num_sms = 0;
     std::mutex tune_mu;
     std::unordered_map<tmg::TuneKey, tm_tuning, tmg::TuneKeyHash> tuned;
+    // serving: device ms one request of a (shape, delta bucket, flavour) takes,
+    // learnt from timed launches and shared by every server of this graph
+    std::mutex cost_mu;
+    std::unordered_map<uint64_t, double> serve_cost_ms;
 };
 
 namespace tmg {
@@ -257,6 +268,10 @@ struct Scratch {
 
 void drop_batches(const tm_graph* g);
 
+// Record the donation counters of a finished count-mode launch for
+// tm_last_search_stats (per calling thread).
+void note_search_stats(const Ctrl& c);
+
 // The query's plan with the graph's cached tuning for its shape applied.
 void query_plan(tm_query* q, Plan* out);
 
@@ -275,6 +290,20 @@ struct LaunchCfg {
     int grid;
     int smem_bytes;      // per block
 };
+
+// Queries that share one persistent launch.  A launch has one frame size and
+// one block size for all its warps, so a query with large frames (a deep motif)
+// would lower the occupancy of every other query of the launch; queries whose
+// own launch shape allows the same resident blocks per SM go together instead.
+struct LaunchGroup {
+    int first, count;    // positions in the grouped order
+    int warp_smem;       // frame bytes per warp (largest of the group)
+    int warps;           // warps per block
+    unsigned feat;       // union of the group's plan features
+};
+// Groups of nq plans for `mode`; order[i] = index of the query at grouped position i.
+std::vector<LaunchGroup> occupancy_groups(const tm_graph* g, Mode mode, const Plan* const* plans, int nq,
+                                          int* order);
 
 // Launch the persistent search over nq queries (qdev already on the device).
 // Ctrl (incl. total_chunks) and qdev must already be initialised on the stream.

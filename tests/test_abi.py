@@ -56,6 +56,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(tmg._Motif) == 4 + 4 + 8 + 8 + 8 + 7 * 8 + 16 + 16 + 4 + 4 * 3 + 4 * 8
     assert ctypes.sizeof(tmg.Tuning) == 16
     assert ctypes.sizeof(tmg._Work) == 8 * (1 + 8 + 8 + 1 + 1)
+    assert ctypes.sizeof(tmg._ServeCfg) == 8 + 4 * 4 + 8 + 8
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
