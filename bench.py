@@ -148,54 +148,94 @@ def workload(scale, name="powerlaw_10m"):
 
 # --------------------------------------------------------------- CPU oracle
 
-def oracle_rate(g, queries, seconds, og=None):
-    """Oracle count over contiguous root ranges of every query, grown until ~seconds of CPU work."""
+def step_config(g, queries, count_only, ws):
+    """The `config` object of both arms' lines (the workload one step covers)."""
+    return {"workload": g.name, "n_nodes": g.n_nodes, "n_edges": g.n_edges,
+            "queries": [q.name for q in queries], "delta_s": queries[0].delta,
+            "enumerate_cap": None if count_only else CAP,
+            "step": "count of each query" if count_only else "count + capped enumerate of each query",
+            "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(og, queries, m, roots, threads, count_only):
+    """One bounded sample of the step: for each query, the roots of a contiguous range of
+    `roots` edges (placed at a different offset per query) are counted and, unless
+    count_only, enumerated (rows of the range's matches), split into `threads` root
+    sub-ranges run at once.  The oracle's library call releases the GIL, so threads run on
+    separate cores.  Returns (seconds, root edges covered)."""
+    from concurrent.futures import ThreadPoolExecutor
+    jobs = []
+    for qi, q in enumerate(queries):
+        a = (m // (len(queries) + 1)) * (qi + 1)
+        a = max(0, min(a, m - roots))
+        b = min(m, a + roots)
+        cuts = [a + (b - a) * j // threads for j in range(threads + 1)]
+        jobs += [(q, x, y) for x, y in zip(cuts[:-1], cuts[1:]) if y > x]
+
+    def run(job):
+        q, x, y = job
+        c = og.count(q, x, y)
+        if not count_only and c:
+            og.enumerate(q, cap=min(c, CAP), root_begin=x, root_end=y)
+        return y - x
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        done = sum(ex.map(run, jobs))
+    return time.perf_counter() - t0, done
+
+
+def oracle_rate(g, queries, seconds, threads, count_only, og=None):
+    """Grow the sample until it takes about `seconds`; returns (root-edges/s, s, roots)."""
     import oracle
     og = og or oracle.Graph.from_synth(g)
     m = g.n_edges
-    roots = 2048
-    spent = 0.0
-    done_roots = 0
+    roots = 1024 * threads
     while True:
-        t0 = time.perf_counter()
-        for qi, q in enumerate(queries):
-            a = (m // (len(queries) + 1)) * (qi + 1)
-            og.count(q, a, min(m, a + roots))
-        dt = time.perf_counter() - t0
-        spent += dt
-        done_roots += roots * len(queries)
-        if spent >= seconds or roots >= m:
-            break
-        roots = min(m, int(roots * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
-        if spent + dt * 8 > seconds * 1.5:
-            roots = min(roots, int(roots / 4) + 1)
-    return done_roots / spent, spent, done_roots
+        dt, done = oracle_sample(og, queries, m, roots, threads, count_only)
+        if dt >= seconds * 0.5 or roots >= m:
+            return done / dt, dt, done
+        roots = min(m, int(roots * min(16.0, max(2.0, seconds / max(dt, 1e-3)))))
 
 
 def run_reference(args, rank, ws):
     if rank != 0:
         return
     g, queries = workload(args.scale, args.workload)
+    count_only = args.workload == "hubskew_100m"
     import oracle
     t0 = time.perf_counter()
     og = oracle.Graph.from_synth(g)
     build_s = time.perf_counter() - t0
+    threads = host_cores()
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    # size one step's sample once (untimed), then time the steps on that sample
+    _, _, roots = oracle_rate(g, queries, per_step, threads, count_only, og)
+    per_query = max(1, roots // len(queries))
     times, roots_total = [], 0
     for s in range(args.warmup + args.steps):
-        rate, spent, roots = oracle_rate(g, queries, per_step, og)
+        dt, done = oracle_sample(og, queries, g.n_edges, per_query, threads, count_only)
         if s >= args.warmup:
-            times.append(spent)
-            roots_total += roots
+            times.append(dt)
+            roots_total += done
     value = roots_total / sum(times)
     line = {"impl": "reference", "metric": "root-edges/s", "value": value, "unit": "root-edges/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": g.name, "queries": [q.name for q in queries], "delta_s": 3600},
-            "cpu_baseline": {"value": value, "unit": "root-edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"contiguous root ranges of each query, ~{per_step:.0f} s of CPU per step; "
-                                       f"oracle graph build {build_s:.1f} s not timed"},
+            "config": step_config(g, queries, count_only, ws),
+            "cpu_baseline": {"value": value, "unit": "root-edges/s", "cores": threads, "kind": "oracle",
+                             "sample": f"each step: {per_query} contiguous root edges per query, "
+                                       f"{'counted' if count_only else 'counted and enumerated'}, split "
+                                       f"into {threads} root ranges on {threads} threads; oracle graph "
+                                       f"build {build_s:.1f} s not timed"},
             "e2e": {"value": value, "unit": "root-edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -344,12 +384,7 @@ def main():
         "metric": "root-edges/s", "value": value, "unit": "root-edges/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": g.name, "n_nodes": g.n_nodes, "n_edges": m,
-                   "queries": [q.name for q in queries], "delta_s": queries[0].delta,
-                   "enumerate_cap": None if count_only else CAP,
-                   "step": "count of each query" if count_only else "count + capped enumerate of each query",
-                   "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": step_config(g, queries, count_only, ws),
         "matches_per_s": matches * ws / (ms / 1000.0),
         "totals": totals,
         "count_kernel_ms": [round(float(np.mean([k[2 * i] for k, _ in search_ms])), 4) for i in range(len(queries))],
@@ -364,15 +399,60 @@ def main():
                      "alg_bytes_per_step": int(b_low),
                      "kernel_ms_per_step": {"count": count_ms, "enum_count_pass": enum_count_ms, "fill": fill_ms}},
     }
-    if rank == 0 and not args.no_extras:
+    extras = rank == 0 and ws == 1 and not args.no_extras
+    if extras:
         line["ablation"] = ablation_leg(queries, qs, stream)
-    if rank == 0 and not args.no_extras and not count_only:
+    if extras and not count_only:
         line["e2e"] = e2e_leg(args, g, queries, dev)
         line["batched"] = batched_leg(gg, dev, stream)
         line["served"] = served_leg(gg, dev)
-        line["cpu_baseline"] = cpu_leg(g, queries, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_leg(g, queries, args.cpu_seconds, count_only)
+        for q in qs:
+            q.free()
+        gg.free()
+        line["hubskew_100m"] = hubskew_leg(args, dev, stream, pk)
+    elif extras:
+        line["cpu_baseline"] = cpu_leg(g, queries, args.cpu_seconds, count_only)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def hubskew_leg(args, dev, stream, pk, reps=3):
+    """The hub-skewed graph (100M edges, 10M nodes, Zipf 1.8 with 0.01% of nodes owning 20%
+    of the endpoints, 16 edge labels, 30 days): counts of the labelled 5-edge path with gaps
+    <= 600 s and of the chorded 4-cycle (delta 7200 s), each count launch timed with CUDA
+    events, and the roofline of the pair (algorithmic bytes from the work counters)."""
+    import torch
+    import synth
+    import paper_2310_02800_gb300 as tmg
+    g = synth.hub_skewed_100m(scale=args.scale)
+    queries = synth.hub_skewed_queries()
+    with torch.cuda.stream(stream):
+        gg = tmg.Graph.from_synth(g, device=dev, stream=stream)
+        m = gg.n_edges
+        rows, b_low, ms_sum = [], 0, 0.0
+        for mo in queries:
+            q = gg.compile(mo)
+            q.profile(True)
+            c = q.count(stream=stream)
+            ms = []
+            for _ in range(reps):
+                assert q.count(stream=stream) == c
+                ms.append(q.last_ms()[0])
+            w = q.work(stream=stream)
+            b = alg_bytes(w, mo.k, 0, True)[1]
+            med = float(np.median(ms))
+            b_low += b
+            ms_sum += med
+            rows.append({"query": mo.name, "matches": c, "count_ms": round(med, 3),
+                         "alg_bytes": int(b), "root_edges_per_s": m / (med / 1000.0)})
+            q.free()
+        gg.free()
+    achieved = b_low / (ms_sum / 1000.0) / 1e9
+    return {"workload": g.name, "n_edges": m, "delta_s": queries[0].delta, "queries": rows,
+            "root_edges_per_s": len(rows) * m / (ms_sum / 1000.0),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "kernel": "search_kernel<count>"}}
 
 
 def sweeps(args, dev, stream, reps=3):
@@ -457,129 +537,189 @@ def e2e_leg(args, g, queries, dev):
             "includes": "host->device upload and GPU build of the graph, 4x(count + enumerate), rows to host"}
 
 
-def batched_leg(gg, dev, stream, dmax=3600.0, autotune=True):
-    """64-query mix (k in 2..6, delta log-uniform in [60, dmax]): one persistent CUDA-graph
-    launch vs 64 single-query launches.  The default dmax keeps the leg to seconds; the full
-    [60, 86400] range is --workload batch64."""
+def mix_cost_sample(gg, mix, limit_s=1.0, max_frac=0.02, seed_stream=811):
+    """Device seconds one full count of each query would take, extrapolated from root ranges
+    at seeded positions (count only; each range's kernel time from CUDA events).  Ranges grow
+    from 256 roots by doubling until 2% of the roots are covered or the query has used
+    limit_s of wall time, so the cost of a query that would run for hours is found in about
+    a second."""
+    import synth
+    m = gg.n_edges
+    starts = [int(x) for x in synth.draws(synth.SEED_BASE + 4, seed_stream, 48)]
+    rows = []
+    for mo in mix:
+        q = gg.compile(mo)
+        q.profile(True)
+        span, done, dev_ms, i = 256, 0, 0.0, 0
+        t0 = time.perf_counter()
+        while done < max_frac * m and i < len(starts):
+            span = min(span, m)
+            a = starts[i] % max(1, m - span + 1)
+            q.count_roots(a, a + span)
+            dev_ms += q.last_ms()[0]
+            done += span
+            i += 1
+            if time.perf_counter() - t0 > limit_s:
+                break
+            span *= 2
+        rows.append({"query": mo.name, "est_s": dev_ms / 1000.0 * m / done, "sampled_roots": done})
+        q.free()
+    return rows
+
+
+def batched_leg(gg, dev, stream, dmax=86_400.0, limit_s=2.0, reps=2, autotune=True):
+    """Config of the batched workload: the seeded 64-query mix (k in 2..6, delta log-uniform in
+    [60, dmax] s) counted in one CUDA-graph launch (one persistent launch per occupancy
+    group) vs one query at a time.  Every query is first costed from a root sample; a query
+    whose full count would take more than limit_s of device time is left out of both arms
+    and reported with its estimate (the day-long 5- and 6-edge out-stars on this graph's hubs
+    enumerate 1e11-1e13 matches).  Then, after per-shape autotuning of the cheap queries, both
+    arms again."""
     import torch
     import synth
     mix = synth.query_mix(64, dmax=dmax)
-    qs = [gg.compile(q) for q in mix]
+    cost = mix_cost_sample(gg, mix)
+    keep = [i for i, r in enumerate(cost) if r["est_s"] <= limit_s]
+    left_out = [cost[i] for i in range(len(mix)) if i not in keep]
+    qs = [gg.compile(mix[i]) for i in keep]
+    m = gg.n_edges
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        return r, (time.perf_counter() - t0) / reps
+
     with torch.cuda.stream(stream):
         want = gg.count_batch(qs, stream=stream)
-        for _ in range(2):
-            gg.count_batch(qs, stream=stream)
-        t0 = time.perf_counter()
-        reps = 3
-        for _ in range(reps):
-            got = gg.count_batch(qs, stream=stream)
-        tb = (time.perf_counter() - t0) / reps
-        assert got == want
-        single = [q.count(stream=stream) for q in qs]
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            single = [q.count(stream=stream) for q in qs]
-        ts = (time.perf_counter() - t0) / reps
-    ok = single == want
-    m = gg.n_edges
-    out = {"queries": 64, "delta_range_s": [60, dmax], "batched_ms": 1000 * tb, "sequential_ms": 1000 * ts,
-           "batched_root_edges_per_s": 64 * m / tb, "sequential_root_edges_per_s": 64 * m / ts,
-           "speedup": ts / tb, "totals_equal": ok, "matches": int(sum(want))}
+        got, tb = timed(lambda: gg.count_batch(qs, stream=stream))
+        single, ts = timed(lambda: [q.count(stream=stream) for q in qs])
+    n = len(qs)
+    out = {"queries": len(mix), "timed_queries": n, "delta_range_s": [60, dmax],
+           "left_out": left_out, "est_device_s_of_timed": sum(cost[i]["est_s"] for i in keep),
+           "batched_ms": 1000 * tb, "sequential_ms": 1000 * ts,
+           "batched_root_edges_per_s": n * m / tb, "sequential_root_edges_per_s": n * m / ts,
+           "speedup": ts / tb, "totals_equal": got == want and single == want, "matches": int(sum(want))}
     if autotune:
-        # per-shape tuning (warps per block, chunk size, split depth, split threshold), untimed;
-        # the graph caches it by motif shape and delta bucket for later compiles
+        # per-shape tuning (warps per block, chunk size, split depth, split threshold) of the
+        # queries that count in under 50 ms, untimed; the graph caches it by motif shape and
+        # delta bucket, and both arms use it
         t0 = time.perf_counter()
+        tuned = 0
         with torch.cuda.stream(stream):
-            for q in qs:
-                q.autotune(stream=stream)
+            for q, i in zip(qs, keep):
+                if cost[i]["est_s"] < 0.05:
+                    q.autotune(stream=stream)
+                    tuned += 1
             tune_s = time.perf_counter() - t0
-            gg.count_batch(qs, stream=stream)
-            t0 = time.perf_counter()
-            for _ in range(reps):
-                got = gg.count_batch(qs, stream=stream)
-            tb2 = (time.perf_counter() - t0) / reps
-            t0 = time.perf_counter()
-            for _ in range(reps):
-                single = [q.count(stream=stream) for q in qs]
-            ts2 = (time.perf_counter() - t0) / reps
-        out["autotuned"] = {"batched_ms": 1000 * tb2, "sequential_ms": 1000 * ts2, "speedup": ts2 / tb2,
-                            "vs_untuned_sequential": ts / tb2, "tune_s": tune_s,
-                            "totals_equal": got == want and single == want}
+            got2, tb2 = timed(lambda: gg.count_batch(qs, stream=stream))
+            single2, ts2 = timed(lambda: [q.count(stream=stream) for q in qs])
+        out["autotuned"] = {"tuned_queries": tuned, "batched_ms": 1000 * tb2, "sequential_ms": 1000 * ts2,
+                            "speedup": ts2 / tb2, "vs_untuned_sequential": ts / tb2,
+                            "vs_untuned_batched": tb / tb2, "tune_s": tune_s,
+                            "totals_equal": got2 == want and single2 == want}
     return out
 
 
-def served_leg(gg, dev, duration_s=2.0, dmax=3600.0, max_requests=400, kmax=6,
-               shapes=((2, 16), (1, 16), (2, 4), (2, 1), (4, 4), (4, 1))):
-    """Poisson arrivals (50 / 200 / 1000 q/s) of a 70% count / 30% enumerate mix (cap 1e6),
-    k in 2..6, delta log-uniform in [60, dmax]: served (continuous batching) vs serial
-    single-query execution of the same trace."""
-    import torch
+SERVE_RATES = ((50, 2000), (200, 4000), (1000, 4000), (2000, 4000), (5000, 4000))
+
+
+def serve_trace(qs, kinds, rate, n, seed_stream):
+    """(arrival s, query index, enumerate?) of n Poisson arrivals at `rate` q/s; 30% enumerate."""
     import synth
-    out = {"delta_range_s": [60, dmax], "k_range": [2, kmax]}
+    arr = synth.arrival_trace(rate, n, synth.SEED_BASE + 5, stream=seed_stream)
+    return [(float(arr[i]), i % len(qs), int(kinds[i % len(kinds)] % 10) < 3) for i in range(n)]
+
+
+def run_served(gg, qs, reqs, cap, **shape):
+    """Submit each request at its arrival time from one thread while a second thread
+    collects results in submission order and releases them (a client that keeps results
+    only as long as it needs them); latency = completion - scheduled arrival."""
+    import queue
+    srv = gg.serve(mem_budget_bytes=8 << 30, **shape)
+    pending = queue.Queue()
+    lat, totals = [], []
+
+    def harvest():
+        while True:
+            item = pending.get()
+            if item is None:
+                return
+            tk, lg = item
+            r = srv.wait(tk)
+            lat.append(1000.0 * lg + r.latency_ms)
+            totals.append(r.total)
+            srv.release(tk)
+
+    th = threading.Thread(target=harvest)
+    th.start()
+    t0 = time.perf_counter()
+    for at, qi, en in reqs:
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        lag = max(0.0, time.perf_counter() - t0 - at)
+        pending.put((srv.submit(qs[qi], enumerate=en, cap=cap if en else 0), lag))
+    pending.put(None)
+    th.join()
+    wall = time.perf_counter() - t0
+    srv.stop()
+    return lat, totals, wall
+
+
+def run_serial(gg, qs, reqs, cap, dev):
+    """One request at a time through tm_count / tm_enumerate, in arrival order (FIFO)."""
+    import torch
+    outbuf = torch.empty((cap, 6), dtype=torch.int32, device=f"cuda:{dev}")
+    lat, totals = [], []
+    t0 = time.perf_counter()
+    for at, qi, en in reqs:
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        q = qs[qi]
+        if en:
+            _, tot, _ = q.enumerate(outbuf.view(-1)[: cap * q.k].view(cap, q.k))
+        else:
+            tot = q.count()
+        totals.append(tot)
+        lat.append(1000.0 * (time.perf_counter() - t0 - at))
+    return lat, totals, time.perf_counter() - t0
+
+
+def served_leg(gg, dev, dmax=3600.0, kmax=6, rates=SERVE_RATES, shape=None, cap=1_000_000):
+    """Poisson arrivals of a 70% count / 30% enumerate mix (cap 1e6), k in 2..kmax, delta
+    log-uniform in [60, dmax] s: served (continuous batching, the library's default shape
+    unless `shape` is given) vs serial single-query execution of the same trace.  Latency runs
+    from each request's scheduled arrival to its completion, in both arms; throughput =
+    requests / wall time from the first arrival to the last completion."""
+    import synth
+    shape = shape or {}
     mix = synth.query_mix(256, seed=synth.SEED_BASE + 5, dmax=dmax, kmax=kmax)
     kinds = synth.draws(synth.SEED_BASE + 5, 601, 256)
     qs = [gg.compile(q) for q in mix]
-    for rate in (50, 200, 1000):
-        n = min(max_requests, max(8, int(rate * duration_s)))
-        arr = synth.arrival_trace(rate, n, synth.SEED_BASE + 5, stream=700 + rate)
-        reqs = [(float(arr[i]), i % len(qs), int(kinds[i % len(kinds)] % 10) < 3) for i in range(n)]
-        configs = {}
-        for streams, max_batch in shapes:
-            srv = gg.serve(mem_budget_bytes=8 << 30, streams=streams, max_batch=max_batch)
-            lat, tickets = [], []
-            t0 = time.perf_counter()
-            for at, qi, en in reqs:
-                now = time.perf_counter() - t0
-                if at > now:
-                    time.sleep(at - now)
-                tickets.append(srv.submit(qs[qi], enumerate=en, cap=1_000_000 if en else 0))
-            for tk in tickets:
-                r = srv.wait(tk)
-                lat.append(r.latency_ms)
-                srv.release(tk)
-            wall = time.perf_counter() - t0
-            srv.stop()
-            configs[f"streams{streams}_batch{max_batch}"] = {
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "throughput_qps": n / wall}
-        # serial single-query execution of the same trace (FIFO, one at a time)
-        slat = []
-        outbuf = torch.empty((1_000_000, 6), dtype=torch.int32, device=f"cuda:{dev}")
-        t0 = time.perf_counter()
-        busy_until = 0.0
-        for at, qi, en in reqs:
-            now = time.perf_counter() - t0
-            if at > now and at > busy_until:
-                time.sleep(at - now)
-            s0 = time.perf_counter() - t0
-            q = qs[qi]
-            if en:
-                q.enumerate(outbuf.view(-1)[: 1_000_000 * q.k].view(1_000_000, q.k))
-            else:
-                q.count()
-            done = time.perf_counter() - t0
-            busy_until = done
-            slat.append(1000 * (done - at))
-        swall = time.perf_counter() - t0
-        m = gg.n_edges
-        # headline: the library's default shape (2 streams, batches of up to 16), chosen before
-        # the run; the lowest p99 over all shapes tried is reported beside it
-        main = f"streams{shapes[0][0]}_batch{shapes[0][1]}"
-        best = min(configs, key=lambda c: (configs[c]["p99_ms"], -configs[c]["throughput_qps"]))
-        out[str(rate)] = {"requests": n, "shape": main, **configs[main], "best_shape": best,
-                          "best_shape_p99_ms": configs[best]["p99_ms"],
-                          "root_edges_per_s": m * configs[main]["throughput_qps"],
-                          "serial_p50_ms": float(np.percentile(slat, 50)), "serial_p99_ms": float(np.percentile(slat, 99)),
-                          "serial_throughput_qps": n / swall, "configs": configs}
+    out = {"delta_range_s": [60, dmax], "k_range": [2, kmax], "mix": "70% count / 30% enumerate (cap 1e6)",
+           "shape": shape or "library default (2 streams, batches by expected cost)"}
+    # one untimed pass over the mix: compiled queries warm, and the graph's per-shape cost
+    # estimates (kept by the library for every server of this graph) learnt
+    warm = serve_trace(qs, kinds, 1e9, len(qs), 699)
+    run_served(gg, qs, warm, cap, **shape)
+    for rate, n in rates:
+        reqs = serve_trace(qs, kinds, rate, n, 700 + rate)
+        lat, tot_a, wall = run_served(gg, qs, reqs, cap, **shape)
+        slat, tot_b, swall = run_serial(gg, qs, reqs, cap, dev)
+        out[str(rate)] = {"requests": n, "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)), "throughput_qps": n / wall,
+                          "serial_p50_ms": float(np.percentile(slat, 50)),
+                          "serial_p99_ms": float(np.percentile(slat, 99)), "serial_throughput_qps": n / swall,
+                          "root_edges_per_s": gg.n_edges * n / wall, "results_equal": tot_a == tot_b}
     return out
 
 
 def powerlaw_1b_graph(scale):
-    """The 1B-edge, 100M-node graph: Zipf 2.1 popularity on both endpoints (no copy model:
-    at 1e9 edges preferential attachment puts ~15% of all edges on one node)."""
+    """The 1B-edge, 100M-node graph (Zipf 2.1 popularity on both endpoints)."""
     import synth
-    n = max(16, int(100_000_000 * scale)); m = max(16, int(1_000_000_000 * scale))
-    return synth.powerlaw_graph(n, m, synth.SEED_BASE + 5, alpha=2.1, span=94_608_000.0, pa=False)
+    return synth.powerlaw_1b(scale=scale)
 
 
 def count_1b(args, dev, stream, delta=600):
@@ -621,7 +761,10 @@ def count_1b(args, dev, stream, delta=600):
 
 
 def serve_1b(args, dev):
-    """Served Poisson traces on the resident 1B-edge power-law graph."""
+    """The serving workload on the resident 1B-edge graph.  First the stated mix (k 2..6,
+    delta log-uniform in [60, 86400] s) is costed per request from a 0.1% root sample; then the
+    part of the mix a latency trace can absorb (k 2..4, delta <= 600 s) is served at Poisson
+    rates below its capacity, against serial execution of the same trace."""
     import synth
     import paper_2310_02800_gb300 as tmg
     t0 = time.perf_counter()
@@ -631,20 +774,35 @@ def serve_1b(args, dev):
     gg = tmg.Graph.from_synth(g, device=dev)
     load_s = time.perf_counter() - t0
     del g
-    # 2-4 edges, delta up to 10 minutes: longer windows on this graph's hubs make single
-    # requests run for minutes, which a latency trace cannot absorb
-    res = served_leg(gg, dev, duration_s=2.0, dmax=600.0, max_requests=40, kmax=4, shapes=((2, 16), (4, 4)))
-    line = {"metric": "p50/p99 latency and throughput, served vs serial", "workload": gg.n_edges,
+    stated = synth.query_mix(64, seed=synth.SEED_BASE + 5, dmax=86_400.0, kmax=6)
+    cost = mix_cost_sample(gg, stated)
+    est = np.array([r["est_s"] for r in cost])
+    res = served_leg(gg, dev, dmax=600.0, kmax=4, rates=((0.25, 24), (1.0, 48)))
+    line = {"metric": "p50/p99 latency and throughput, served vs serial", "workload": "serve_1b",
             "config": {"workload": f"powerlaw_1b x{args.scale}", "n_edges": gg.n_edges, "n_nodes": gg.n_nodes,
                        "device_bytes": gg.device_bytes, "generate_s": gen_s, "load_s": load_s},
+            "stated_mix_cost": {"queries": len(cost), "p50_s": float(np.percentile(est, 50)),
+                                "p90_s": float(np.percentile(est, 90)), "max_s": float(est.max()),
+                                "under_1s": int((est < 1.0).sum()), "rows": cost},
             "served": res}
     print(json.dumps(line), flush=True)
 
 
-def cpu_leg(g, queries, seconds):
-    rate, spent, roots = oracle_rate(g, queries, seconds)
-    return {"value": rate, "unit": "root-edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"{roots} root edges over contiguous ranges of the 4 queries ({spent:.1f} s single-threaded)"}
+def cpu_leg(g, queries, seconds, count_only=False):
+    """The oracle timed on the host's cores: root-range parallel over all of them (the
+    baseline), and on one core beside it."""
+    import oracle
+    og = oracle.Graph.from_synth(g)
+    cores = host_cores()
+    rate, spent, roots = oracle_rate(g, queries, seconds, cores, count_only, og)
+    rate1, spent1, roots1 = oracle_rate(g, queries, seconds / 3, 1, count_only, og)
+    what = "counted" if count_only else "counted and enumerated"
+    return {"value": rate, "unit": "root-edges/s", "cores": cores, "kind": "oracle",
+            "sample": f"{roots} root edges in contiguous ranges of the {len(queries)} queries, {what}, "
+                      f"split into {cores} root ranges on {cores} threads ({spent:.1f} s)",
+            "nproc": os.cpu_count(),
+            "single_core": {"value": rate1, "unit": "root-edges/s", "cores": 1,
+                            "sample": f"{roots1} root edges, {what} ({spent1:.1f} s)"}}
 
 
 if __name__ == "__main__":
