@@ -588,9 +588,15 @@ std::vector<LaunchGroup> occupancy_groups(const tm_graph* g, Mode mode, const Pl
         wpb[j] = c.warps_per_block;
         order[j] = j;
     }
-    // highest occupancy first; arrival order within a group
+    // highest occupancy first; within a group the likely most expensive queries
+    // (more motif edges, then longer delta) first: a persistent launch claims
+    // root chunks in query order, so the cheap queries fill the tails of the
+    // expensive ones instead of the other way round
     std::stable_sort(order, order + nq, [&](int a, int b) {
-        return grid[a] != grid[b] ? grid[a] > grid[b] : wpb[a] > wpb[b];
+        if (grid[a] != grid[b]) return grid[a] > grid[b];
+        if (wpb[a] != wpb[b]) return wpb[a] > wpb[b];
+        if (plans[a]->k != plans[b]->k) return plans[a]->k > plans[b]->k;
+        return plans[a]->delta > plans[b]->delta;
     });
     std::vector<LaunchGroup> out;
     for (int i = 0; i < nq; ++i) {
