@@ -537,10 +537,10 @@ def e2e_leg(args, g, queries, dev):
             "includes": "host->device upload and GPU build of the graph, 4x(count + enumerate), rows to host"}
 
 
-def mix_cost_sample(gg, mix, limit_s=1.0, max_frac=0.02, seed_stream=811):
+def mix_cost_sample(gg, mix, limit_s=1.0, max_frac=0.02, seed_stream=811, first_span=256):
     """Device seconds one full count of each query would take, extrapolated from root ranges
     at seeded positions (count only; each range's kernel time from CUDA events).  Ranges grow
-    from 256 roots by doubling until 2% of the roots are covered or the query has used
+    from first_span roots by doubling until 2% of the roots are covered or the query has used
     limit_s of wall time, so the cost of a query that would run for hours is found in about
     a second."""
     import synth
@@ -550,7 +550,7 @@ def mix_cost_sample(gg, mix, limit_s=1.0, max_frac=0.02, seed_stream=811):
     for mo in mix:
         q = gg.compile(mo)
         q.profile(True)
-        span, done, dev_ms, i = 256, 0, 0.0, 0
+        span, done, dev_ms, i = first_span, 0, 0.0, 0
         t0 = time.perf_counter()
         while done < max_frac * m and i < len(starts):
             span = min(span, m)
@@ -687,7 +687,7 @@ def run_serial(gg, qs, reqs, cap, dev):
     return lat, totals, time.perf_counter() - t0
 
 
-def served_leg(gg, dev, dmax=3600.0, kmax=6, rates=SERVE_RATES, shape=None, cap=1_000_000):
+def served_leg(gg, dev, dmax=3600.0, kmax=6, rates=SERVE_RATES, shape=None, cap=1_000_000, n_mix=256):
     """Poisson arrivals of a 70% count / 30% enumerate mix (cap 1e6), k in 2..kmax, delta
     log-uniform in [60, dmax] s: served (continuous batching, the library's default shape
     unless `shape` is given) vs serial single-query execution of the same trace.  Latency runs
@@ -695,8 +695,8 @@ def served_leg(gg, dev, dmax=3600.0, kmax=6, rates=SERVE_RATES, shape=None, cap=
     requests / wall time from the first arrival to the last completion."""
     import synth
     shape = shape or {}
-    mix = synth.query_mix(256, seed=synth.SEED_BASE + 5, dmax=dmax, kmax=kmax)
-    kinds = synth.draws(synth.SEED_BASE + 5, 601, 256)
+    mix = synth.query_mix(n_mix, seed=synth.SEED_BASE + 5, dmax=dmax, kmax=kmax)
+    kinds = synth.draws(synth.SEED_BASE + 5, 601, n_mix)
     qs = [gg.compile(q) for q in mix]
     out = {"delta_range_s": [60, dmax], "k_range": [2, kmax], "mix": "70% count / 30% enumerate (cap 1e6)",
            "shape": shape or "library default (2 streams, batches by expected cost)"}
@@ -775,9 +775,9 @@ def serve_1b(args, dev):
     load_s = time.perf_counter() - t0
     del g
     stated = synth.query_mix(64, seed=synth.SEED_BASE + 5, dmax=86_400.0, kmax=6)
-    cost = mix_cost_sample(gg, stated)
+    cost = mix_cost_sample(gg, stated, first_span=16, max_frac=0.002)
     est = np.array([r["est_s"] for r in cost])
-    res = served_leg(gg, dev, dmax=600.0, kmax=4, rates=((0.25, 24), (1.0, 48)))
+    res = served_leg(gg, dev, dmax=600.0, kmax=4, rates=((0.25, 24), (1.0, 48)), n_mix=32)
     line = {"metric": "p50/p99 latency and throughput, served vs serial", "workload": "serve_1b",
             "config": {"workload": f"powerlaw_1b x{args.scale}", "n_edges": gg.n_edges, "n_nodes": gg.n_nodes,
                        "device_bytes": gg.device_bytes, "generate_s": gen_s, "load_s": load_s},
