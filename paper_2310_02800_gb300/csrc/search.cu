@@ -222,24 +222,6 @@ struct Search {
         f.tspan(s) = d < (uint64_t)SPAN_FAR ? (uint32_t)d : SPAN_FAR;
     }
 
-    // A child window just located is read when its frame is drained, some
-    // steps later: ask L2 for the first line of its time and neighbour
-    // columns now (no register result, nothing waits on it).
-    __device__ void prefetch_window(uint32_t bw) const {
-#ifdef TM_PREFETCH
-        const uint32_t pos = bw & POSMASK;
-        if (bw & PAIRLIST) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(g.pt + pos));
-        } else {
-            const int dir = (bw & INLIST) ? 1 : 0;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(g.at[dir] + pos));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(g.anbr[dir] + pos));
-        }
-#else
-        (void)bw;
-#endif
-    }
-
     __device__ Frame frame(int i) const {
         return Frame{wbase + (MODE == MODE_FILL ? q->plan.lv[i].frame_off_fill : q->plan.lv[i].frame_off)};
     }
@@ -600,7 +582,6 @@ struct Search {
             set_tend(c, s, ct, tend);
             c.beg(s) = cbeg;
             c.len(s) = clen;
-            prefetch_window(cbeg);
             c.root(s) = root;
             if (MODE == MODE_FILL) {
                 for (int j = 0; j < i; ++j) c.eid(nb_c, j, s) = f.eid(nb, j, p);
@@ -754,7 +735,6 @@ struct Search {
                     set_tend(c, sl, tt, tend);
                     c.beg(sl) = cbeg;
                     c.len(sl) = clen;
-                    prefetch_window(cbeg);
                     c.root(sl) = (uint32_t)r;
                     if (MODE == MODE_FILL) c.eid(2, 0, sl) = (int32_t)r;
                     for (int a = 0; ANTI && a < pl.n_anti; ++a)

@@ -166,12 +166,14 @@ def time_windows(t: np.ndarray, n_windows: int, frac: float, seed: int, stream: 
     width = max(1, int((tmax - tmin) * per / m))
     slots = max(1, (tmax - tmin) // width)
     picks = sorted(set(int(x % slots) for x in draws(seed, stream, 4 * n_windows)))[:n_windows]
-    out = []
-    for p in picks:
-        t0 = tmin + p * width
-        t1 = t0 + width
-        out.append((t0, t1, int(np.count_nonzero(t < t0)), int(np.count_nonzero(t < t1))))
-    return out
+    # edges per width-wide time slot, in one pass over the times (chunked to bound memory)
+    per_slot = np.zeros(slots + 1, np.int64)
+    for c in range(0, m, 1 << 26):
+        b = np.minimum((t[c:c + (1 << 26)] - tmin) // width, slots)
+        per_slot += np.bincount(b, minlength=slots + 1)
+    before = np.concatenate([[0], np.cumsum(per_slot)])
+    return [(tmin + p * width, tmin + (p + 1) * width, int(before[p]), int(before[p + 1])) for p in picks]
+
 
 
 # ------------------------------------------------------------------ motifs
