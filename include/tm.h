@@ -190,6 +190,28 @@ tm_status tm_count_roots(tm_graph* g, tm_query* q, int64_t root_begin, int64_t r
 tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_t* match_dev, uint64_t cap,
                        uint64_t* n_written, uint64_t* total);
 
+/* Enumerate nq queries together (Section 2.1 enumeration flavour, many
+ * queries at once): one multi-query count pass (per-chunk counts of every
+ * query), a per-query scan of those counts into row offsets, and one
+ * multi-query fill pass that writes each query's rows from the offsets on the
+ * device, with a single stream synchronisation at the end.  Queries are grouped
+ * by the occupancy their launch shape allows (one persistent launch per group
+ * and pass).  Per query j (all arrays have nq entries):
+ *   match_devs[j] : device pointer int32[caps[j] * k_j] (may be NULL if caps[j] == 0)
+ *   caps[j]       : rows available (host array)
+ *   n_written[j], totals[j] : host arrays; receive min(total, cap) and the exact total
+ * Rows are as for tm_enumerate (the lexicographically first min(cap, total)).
+ *   kernel_ms : host double[2] or NULL; receives the device time of the count
+ *               launches and of the fill launches (CUDA events on the stream)
+ * Returns TM_E_TRUNCATED (non-fatal) when any query had more matches than its
+ * cap, TM_E_INVALID for nq outside [1, 4096] or a query given twice.  Uses each
+ * query's own scratch (as tm_enumerate does) and batch buffers cached on the
+ * graph by batch shape; calls with the same shape from two host threads are
+ * serialised.  On TM_E_TIMEOUT the outputs are untouched but rows may have been
+ * written.  Synchronises the stream. */
+tm_status tm_enumerate_batch(tm_graph* g, tm_query* const* qs, int nq, void* stream, int32_t* const* match_devs,
+                             const uint64_t* caps, uint64_t* n_written, uint64_t* totals, double* kernel_ms);
+
 /* Count nq queries in one persistent launch (replayed from a captured CUDA
  * graph).  totals: host pointer uint64[nq].  Queries may differ in size,
  * shape, delta and constraints.  Synchronises the stream. */

@@ -90,6 +90,7 @@ _SIGS = [
     ("tm_count_roots", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _U64P, _P]),
     ("tm_enumerate", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_uint64, _U64P, _U64P]),
     ("tm_count_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    ("tm_enumerate_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     ("tm_count_batch_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     ("tm_autotune", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Tuning)]),
     ("tm_count_baseline", ctypes.c_int, [_P, _P, _P, _U64P, ctypes.POINTER(ctypes.c_double)]),
@@ -257,6 +258,23 @@ class Graph:
         out = np.zeros(len(queries), np.uint64)
         _check(lib().tm_count_batch(self._h, arr, len(queries), _stream_ptr(stream), out.ctypes.data))
         return [int(x) for x in out]
+
+    def enumerate_batch(self, queries, outs, stream=None, timed=False):
+        """Enumerate several queries together (tm_enumerate_batch).  outs[j]: int32 CUDA tensor
+        [cap_j, k_j] (or None for a count only).  Returns (n_written, totals, truncated) lists /
+        flag, plus (count ms, fill ms) when timed."""
+        n = len(queries)
+        arr = (ctypes.c_void_p * n)(*[q._h.value for q in queries])
+        bufs = (ctypes.c_void_p * n)(*[None if o is None else _ptr(o) for o in outs])
+        caps = np.array([0 if o is None else int(o.shape[0]) for o in outs], np.uint64)
+        nw = np.zeros(n, np.uint64)
+        tot = np.zeros(n, np.uint64)
+        ms = (ctypes.c_double * 2)()
+        st = _check(lib().tm_enumerate_batch(self._h, arr, n, _stream_ptr(stream), bufs, caps.ctypes.data,
+                                             nw.ctypes.data, tot.ctypes.data, ms if timed else None),
+                    allow=(OK, E_TRUNCATED))
+        res = ([int(x) for x in nw], [int(x) for x in tot], st == E_TRUNCATED)
+        return res + ((ms[0], ms[1]),) if timed else res
 
     def count_batch_noalloc(self, queries, totals, stream=None):
         """Batched count that allocates nothing: totals is a caller-owned uint64/int64 CUDA tensor

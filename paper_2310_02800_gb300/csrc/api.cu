@@ -618,7 +618,9 @@ std::vector<LaunchGroup> occupancy_groups(const tm_graph* g, Mode mode, const Pl
 // order.
 struct BatchExec {
     int nq = 0;
+    Mode mode = MODE_COUNT;                    // the pass its launches run
     std::vector<LaunchGroup> groups;
+    cudaEvent_t ev[2] = {nullptr, nullptr};    // optional timing of its launches
     char* head = nullptr;                      // device: Ctrl[groups] + QueryDev[nq]
     char* stage = nullptr;                     // pinned mirror
     unsigned long long* counters = nullptr;    // device totals, by the caller's query index
@@ -631,8 +633,8 @@ struct BatchExec {
     size_t head_bytes() const { return ctrl_bytes() + (size_t)nq * sizeof(QueryDev); }
     QueryDev* qdev_stage() const { return (QueryDev*)(stage + ctrl_bytes()); }
     QueryDev* qdev_dev() const { return (QueryDev*)(head + ctrl_bytes()); }
-    bool same_shape(int n, const std::vector<LaunchGroup>& gs) const {
-        if (n != nq || gs.size() != groups.size()) return false;
+    bool same_shape(int n, const std::vector<LaunchGroup>& gs, Mode md = MODE_COUNT) const {
+        if (n != nq || gs.size() != groups.size() || md != mode) return false;
         for (size_t i = 0; i < gs.size(); ++i)
             if (gs[i].count != groups[i].count || gs[i].warp_smem != groups[i].warp_smem ||
                 gs[i].warps != groups[i].warps || gs[i].feat != groups[i].feat)
@@ -655,6 +657,8 @@ struct BatchExec {
         return s;
     }
     void release() {
+        for (auto& e : ev)
+            if (e) { cudaEventDestroy(e); e = nullptr; }
         if (exec) cudaGraphExecDestroy(exec);
         if (head) cudaFree(head);
         if (counters) cudaFree(counters);
@@ -677,6 +681,20 @@ struct BatchExec {
 
 static std::mutex g_batch_mu;
 static std::map<const tm_graph*, std::vector<std::unique_ptr<BatchExec>>> g_batches;
+
+// The cached executable (buffers, groups, captured graph if any) for one batch shape.
+static BatchExec* cached_exec(const tm_graph* g, int nq, const std::vector<LaunchGroup>& groups, Mode mode) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto& vec = g_batches[g];
+    for (auto& p : vec)
+        if (p->same_shape(nq, groups, mode)) return p.get();
+    vec.emplace_back(new BatchExec());
+    BatchExec* b = vec.back().get();
+    b->nq = nq;
+    b->groups = groups;
+    b->mode = mode;
+    return b;
+}
 
 static tm_status capture_batch(tm_graph* g, BatchExec* b) {
     cudaStream_t cs;
@@ -725,22 +743,7 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
     }
     std::vector<int> order(nq);
     std::vector<LaunchGroup> groups = occupancy_groups(g, MODE_COUNT, plans.data(), nq, order.data());
-    BatchExec* b = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_batch_mu);
-        auto& vec = g_batches[g];
-        for (auto& p : vec)
-            if (p->same_shape(nq, groups)) {
-                b = p.get();
-                break;
-            }
-        if (!b) {
-            vec.emplace_back(new BatchExec());
-            b = vec.back().get();
-            b->nq = nq;
-            b->groups = groups;
-        }
-    }
+    BatchExec* b = cached_exec(g, nq, groups, MODE_COUNT);
     std::lock_guard<std::mutex> use(b->mu);
     tm_status s = b->alloc();
     if (s != TM_OK) return s;
@@ -780,6 +783,165 @@ extern "C" tm_status tm_count_batch(tm_graph* g, tm_query* const* qs, int nq, vo
     if (sum.err) { set_error("a bounded device wait timed out"); return TM_E_TIMEOUT; }
     for (int j = 0; j < nq; ++j) totals[j] = b->counters_host[j];
     return TM_OK;
+}
+
+extern "C" tm_status tm_enumerate_batch(tm_graph* g, tm_query* const* qs, int nq, void* stream,
+                                        int32_t* const* match_devs, const uint64_t* caps, uint64_t* n_written,
+                                        uint64_t* totals, double* kernel_ms) {
+    if (!g || !qs || nq < 1 || nq > 4096 || !match_devs || !caps || !n_written || !totals) {
+        set_error("bad batch arguments");
+        return TM_E_INVALID;
+    }
+    std::vector<const tm_query*> seen(qs, qs + nq);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+        set_error("a query appears twice in the batch (its chunk counts would be shared)");
+        return TM_E_INVALID;
+    }
+    for (int j = 0; j < nq; ++j)
+        if (!qs[j] || qs[j]->g != g || (caps[j] > 0 && !match_devs[j])) {
+            set_error("null or mismatched query or match buffer in batch");
+            return TM_E_INVALID;
+        }
+    TM_ENTER(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t m = (uint64_t)g->v.m;
+    if (kernel_ms) kernel_ms[0] = kernel_ms[1] = 0.0;
+    if (m == 0) {
+        for (int j = 0; j < nq; ++j) totals[j] = n_written[j] = 0;
+        return TM_OK;
+    }
+    std::vector<const Plan*> plans(nq);
+    std::vector<uint64_t> nch(nq);
+    for (int j = 0; j < nq; ++j) {
+        apply_cached_tuning(g, qs[j]);
+        plans[j] = &qs[j]->plan;
+        nch[j] = n_chunks(m, qs[j]->plan.tune.chunk_roots);
+        // each query's own scratch holds its chunk counts, then their offsets
+        tm_status r = scratch_reserve(&qs[j]->scratch, g->device, 1, 1, nch[j], 0);
+        if (r != TM_OK) return r;
+        TM_CUDA(cudaMemsetAsync(qs[j]->scratch.chunk_cnt, 0, (nch[j] + 1) * 8, st));
+    }
+    // pass 1: per-chunk counts of every query, one persistent launch per occupancy group
+    std::vector<int> order(nq);
+    std::vector<LaunchGroup> cg = occupancy_groups(g, MODE_COUNT, plans.data(), nq, order.data());
+    BatchExec* bc = cached_exec(g, nq, cg, MODE_COUNT);
+    std::lock_guard<std::mutex> lock_c(bc->mu);
+    tm_status s = bc->alloc();
+    if (s != TM_OK) return s;
+    memset(bc->stage, 0, bc->ctrl_bytes());
+    for (size_t gi = 0; gi < cg.size(); ++gi) {
+        uint64_t base = 0;
+        for (int i = cg[gi].first; i < cg[gi].first + cg[gi].count; ++i) {
+            const int j = order[i];
+            QueryDev* qd = bc->qdev_stage() + i;
+            memset(qd, 0, sizeof(QueryDev));
+            qd->plan = qs[j]->plan;
+            qd->root_end = m;
+            qd->n_chunks = nch[j];
+            qd->chunk_base = base;
+            base += nch[j];
+            qd->total = bc->counters + j;
+            qd->chunk_cnt = qs[j]->scratch.chunk_cnt;
+        }
+        ((Ctrl*)bc->stage)[gi].total_chunks = base;
+    }
+    if (kernel_ms && !bc->ev[0])
+        for (auto& e : bc->ev) TM_CUDA(cudaEventCreate(&e));
+    TM_CUDA(cudaMemcpyAsync(bc->head, bc->stage, bc->head_bytes(), cudaMemcpyHostToDevice, st));
+    TM_CUDA(cudaMemsetAsync(bc->counters, 0, (size_t)nq * 8, st));
+    if (kernel_ms) TM_CUDA(cudaEventRecord(bc->ev[0], st));
+    for (size_t gi = 0; gi < cg.size(); ++gi) {
+        Scratch v = bc->view(gi);
+        TM_CUDA(cudaMemsetAsync(bc->ready, 0, DEFAULT_TASK_CAP, st));
+        s = launch_search(g, MODE_COUNT, bc->qdev_dev() + cg[gi].first, cg[gi].count, cg[gi].warp_smem,
+                          cg[gi].warps, cg[gi].feat, &v, st);
+        if (s != TM_OK) return s;
+    }
+    if (kernel_ms) TM_CUDA(cudaEventRecord(bc->ev[1], st));
+    // pass 2: chunk offsets
+    for (int j = 0; j < nq; ++j) {
+        s = exclusive_scan_u64(qs[j]->scratch.chunk_cnt, qs[j]->scratch.chunk_cnt, nch[j] + 1,
+                               qs[j]->scratch.scan_tmp, st);
+        if (s != TM_OK) return s;
+    }
+    // pass 3: rows of the queries with room for some, written from each chunk's
+    // offset on the device (chunks past the cap or without matches are skipped)
+    std::vector<int> fq;
+    for (int j = 0; j < nq; ++j)
+        if (caps[j] > 0) fq.push_back(j);
+    BatchExec* bf = nullptr;
+    std::unique_lock<std::mutex> lock_f;
+    if (!fq.empty()) {
+        const int nf = (int)fq.size();
+        std::vector<const Plan*> fplans(nf);
+        for (int i = 0; i < nf; ++i) fplans[i] = plans[fq[i]];
+        std::vector<int> forder(nf);
+        std::vector<LaunchGroup> fg = occupancy_groups(g, MODE_FILL, fplans.data(), nf, forder.data());
+        bf = cached_exec(g, nf, fg, MODE_FILL);
+        lock_f = std::unique_lock<std::mutex>(bf->mu);
+        s = bf->alloc();
+        if (s != TM_OK) return s;
+        memset(bf->stage, 0, bf->ctrl_bytes());
+        for (size_t gi = 0; gi < fg.size(); ++gi) {
+            uint64_t base = 0;
+            for (int i = fg[gi].first; i < fg[gi].first + fg[gi].count; ++i) {
+                const int j = fq[forder[i]];
+                QueryDev* qd = bf->qdev_stage() + i;
+                memset(qd, 0, sizeof(QueryDev));
+                qd->plan = qs[j]->plan;
+                qd->root_end = m;
+                qd->n_chunks = nch[j];
+                qd->chunk_base = base;
+                base += nch[j];
+                qd->total = bf->counters + i;
+                qd->chunk_off = qs[j]->scratch.chunk_cnt;
+                qd->match_out = match_devs[j];
+                qd->cap = caps[j];
+            }
+            ((Ctrl*)bf->stage)[gi].total_chunks = base;
+        }
+        if (kernel_ms && !bf->ev[0])
+            for (auto& e : bf->ev) TM_CUDA(cudaEventCreate(&e));
+        TM_CUDA(cudaMemcpyAsync(bf->head, bf->stage, bf->head_bytes(), cudaMemcpyHostToDevice, st));
+        if (kernel_ms) TM_CUDA(cudaEventRecord(bf->ev[0], st));
+        for (size_t gi = 0; gi < fg.size(); ++gi) {
+            Scratch v = bf->view(gi);
+            s = launch_search(g, MODE_FILL, bf->qdev_dev() + fg[gi].first, fg[gi].count, fg[gi].warp_smem,
+                              fg[gi].warps, fg[gi].feat, &v, st);
+            if (s != TM_OK) return s;
+        }
+        if (kernel_ms) TM_CUDA(cudaEventRecord(bf->ev[1], st));
+        TM_CUDA(cudaMemcpyAsync(bf->stage, bf->head, bf->ctrl_bytes(), cudaMemcpyDeviceToHost, st));
+    }
+    TM_CUDA(cudaMemcpyAsync(bc->counters_host, bc->counters, (size_t)nq * 8, cudaMemcpyDeviceToHost, st));
+    TM_CUDA(cudaMemcpyAsync(bc->stage, bc->head, bc->ctrl_bytes(), cudaMemcpyDeviceToHost, st));
+    TM_CUDA(cudaStreamSynchronize(st));
+    Ctrl sum;
+    memset(&sum, 0, sizeof sum);
+    for (size_t gi = 0; gi < cg.size(); ++gi) {
+        const Ctrl& c = ((const Ctrl*)bc->stage)[gi];
+        sum.donated += c.donated;
+        sum.q_reserve += c.q_reserve;
+        sum.err |= c.err;
+    }
+    for (size_t gi = 0; bf && gi < bf->groups.size(); ++gi) sum.err |= ((const Ctrl*)bf->stage)[gi].err;
+    note_search_stats(sum);
+    if (sum.err) { set_error("a bounded device wait timed out"); return TM_E_TIMEOUT; }
+    if (kernel_ms) {
+        float a = 0.f, b = 0.f;
+        TM_CUDA(cudaEventElapsedTime(&a, bc->ev[0], bc->ev[1]));
+        if (bf) TM_CUDA(cudaEventElapsedTime(&b, bf->ev[0], bf->ev[1]));
+        kernel_ms[0] = a;
+        kernel_ms[1] = b;
+    }
+    bool truncated = false;
+    for (int j = 0; j < nq; ++j) {
+        totals[j] = bc->counters_host[j];
+        n_written[j] = std::min<uint64_t>(totals[j], caps[j]);
+        truncated |= totals[j] > caps[j];
+    }
+    return truncated ? TM_E_TRUNCATED : TM_OK;
 }
 
 // Release batch executables of a graph (called from tm_graph_free).

@@ -201,6 +201,33 @@ def test_root_ranges_and_tunings(tmg):
         assert np.array_equal(pr[: g.n_edges].cpu().numpy().astype(np.uint64), want_pr)
 
 
+def test_enumerate_batch(tmg):
+    """tm_enumerate_batch: each query's exact total and its lexicographically first rows,
+    equal to the oracle's, for caps above the total, below it (TM_E_TRUNCATED) and zero, in
+    one call; a query given twice is rejected."""
+    g = _powerlaw_small(seed=88, n=5000, m=80_000)
+    og = oracle.Graph.from_synth(g)
+    gg = tmg.Graph.from_synth(g)
+    mix = synth.powerlaw_queries(3600) + synth.query_mix(10, seed=synth.SEED_BASE + 31, dmax=20_000)
+    qs = [gg.compile(mo) for mo in mix]
+    want = [og.count(mo) for mo in mix]
+    caps = [w + 3 if j % 3 == 0 else (max(1, w // 2) if j % 3 == 1 else 0) for j, w in enumerate(want)]
+    outs = [None if c == 0 else torch.full((c, mo.k), -5, dtype=torch.int32, device="cuda")
+            for c, mo in zip(caps, mix)]
+    for rep in range(2):
+        nw, tot, trunc, ms = gg.enumerate_batch(qs, outs, timed=True)
+        assert tot == want
+        assert nw == [min(w, c) for w, c in zip(want, caps)]
+        assert trunc == any(w > c for w, c in zip(want, caps))
+        assert ms[0] > 0
+        for mo, o, c, n in zip(mix, outs, caps, nw):
+            if c:
+                rows, _ = og.enumerate(mo, cap=c)
+                assert np.array_equal(o[:n].cpu().numpy(), rows), (mo.name, rep)
+    with pytest.raises(tmg.TMError):
+        gg.enumerate_batch([qs[0], qs[0]], [None, None])
+
+
 def test_donation_on_a_hub(tmg):
     """A few hubs with thousands of edges inside one window: donation to idle warps must not
     lose or duplicate work (split at every level, threshold 0)."""
