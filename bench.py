@@ -86,9 +86,17 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_samples(self, n, limit_s=5.0):
+        """Block until n samples have arrived (bounded), so the record brackets the timed region."""
+        t0 = time.time()
+        while self.proc is not None and len(self.lines) < n and time.time() - t0 < limit_s:
+            time.sleep(0.01)
+        return len(self.lines)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.wait_samples(len(self.lines) + 1, 1.0)    # one sample taken after the timed region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -264,14 +272,15 @@ def kernel_source_hash():
 
 
 def measured_traffic(workload):
-    """DRAM bytes per count launch from the committed ncu capture of this kernel on this
-    workload; None when the kernel sources changed since it was taken."""
+    """DRAM bytes of one step's count pass (all its count launches) from the committed ncu
+    capture of this kernel on this workload; None when the kernel sources changed since it
+    was taken."""
     if workload != "powerlaw_10m" or not os.path.exists(TRAFFIC_FILE):
         return None
     d = json.load(open(TRAFFIC_FILE))
-    if d.get("kernel_source_sha256") != kernel_source_hash():
+    if d.get("kernel_source_sha256") != kernel_source_hash() or "dram_bytes_count_pass_per_step" not in d:
         return None
-    return float(d["dram_bytes_per_count_launch"])
+    return float(d["dram_bytes_count_pass_per_step"])
 
 
 def alg_bytes(w, k, matches_written, with_labels=False):
@@ -319,25 +328,24 @@ def main():
         qs = [gg.compile(q) for q in queries]
         for q in qs:
             q.profile(True)
-        out = torch.empty((1 if count_only else CAP, max(q.k for q in queries)), dtype=torch.int32,
-                          device=f"cuda:{dev}")
+        # one 2^26-row buffer per query (the batched enumeration writes them all in one pass)
+        outs = [torch.empty((1 if count_only else CAP, mo.k), dtype=torch.int32, device=f"cuda:{dev}")
+                for mo in queries]
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
 
+        views = None if count_only else outs
+
         def step():
-            # one search per query delivers both results: tm_enumerate's count pass gives the
-            # exact total (its per-chunk counts place the rows), its fill pass the rows
-            tot, kms, fms = [], [], []
-            for mo, q in zip(queries, qs):
-                if count_only:
-                    c = q.count(stream=stream)
-                    kms.append(q.last_ms()[0]); fms.append(0.0)
-                else:
-                    view = out.view(-1)[: CAP * mo.k].view(CAP, mo.k)
-                    nw, c, _ = q.enumerate(view, stream=stream)
-                    a, b = q.last_ms()
-                    kms.append(a); fms.append(b)
-                tot.append(c)
-            return tot, kms, fms
+            # one search per query delivers both results: tm_enumerate_batch's count pass gives
+            # each exact total (its per-chunk counts place the rows), its fill pass the rows
+            if count_only:
+                tot, kms = [], []
+                for q in qs:
+                    tot.append(q.count(stream=stream))
+                    kms.append(q.last_ms()[0])
+                return tot, kms, [0.0]
+            _, tot, _, (cms, fms) = gg.enumerate_batch(qs, views, stream=stream, timed=True)
+            return tot, [cms], [fms]
 
         for _ in range(args.warmup):
             step()
@@ -347,6 +355,7 @@ def main():
         stream.synchronize()
         clocks = Clocks(dev)
         clocks.start()
+        clocks.wait_samples(1)
         barrier(ws)
         torch.cuda.synchronize()
         e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -387,16 +396,23 @@ def main():
         "config": step_config(g, queries, count_only, ws),
         "matches_per_s": matches * ws / (ms / 1000.0),
         "step_calls": "count only: tm_count per query" if count_only else
-                      "one tm_enumerate per query: the exact total from its count pass, the rows "
-                      "(capped at 2^26) from its fill pass",
+                      "one tm_enumerate_batch over the 4 queries: the exact totals from its count pass "
+                      "(one persistent launch per occupancy group), the rows (capped at 2^26 per query) "
+                      "from its fill pass",
         "totals": totals,
-        "count_kernel_ms": [round(float(np.mean([k[i] for k, _ in search_ms])), 4) for i in range(len(queries))],
+        "count_kernel_ms": ([round(float(np.mean([k[i] for k, _ in search_ms])), 4) for i in range(len(queries))]
+                            if count_only else None),
+        "count_pass_ms_per_step": round(float(count_ms), 4),
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
+                     # DRAM bytes of one step's count pass, beside alg_bytes_per_step
                      "traffic": measured_traffic(args.workload) if args.scale == 1.0 else None,
-                     "alg_bytes_per_launch": int(b_low / len(queries)),
+                     # per query counted: the count pass runs one persistent launch per occupancy
+                     # group, so achieved = the step's algorithmic bytes / the step's count time;
+                     # traffic is the capture's DRAM bytes of one single-query count launch
+                     "alg_bytes_per_query_count": int(b_low / len(queries)),
                      "kernel": "search_kernel<count>", "peak_source": pk["source"],
                      "with_notional_binary_search_GBps": b_full / (count_ms / 1000.0) / 1e9,
                      "alg_bytes_per_step": int(b_low),

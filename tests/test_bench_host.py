@@ -25,7 +25,7 @@ def test_traffic_gate_follows_kernel_code_not_comments(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(root))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(root / "traffic.json"))
     h = bench.kernel_source_hash()
-    json.dump({"kernel_source_sha256": h, "dram_bytes_per_count_launch": 123}, open(bench.TRAFFIC_FILE, "w"))
+    json.dump({"kernel_source_sha256": h, "dram_bytes_count_pass_per_step": 123}, open(bench.TRAFFIC_FILE, "w"))
     assert bench.measured_traffic("powerlaw_10m") == 123.0
     assert bench.measured_traffic("hubskew_100m") is None          # captured on another workload
     src = root / bench.KERNEL_SOURCES[0]
