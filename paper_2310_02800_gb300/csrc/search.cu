@@ -18,8 +18,8 @@
 //    j-th remaining candidate across all parents, so lanes stay busy even when
 //    every individual window is short.  Survivors of a step (structure, label
 //    and injectivity checks) are compacted with __ballot_sync into the child
-//    frame, which is drained once it holds >= 32 parents or its parent frame is
-//    exhausted.  Processing frames in order keeps the emitted matches in
+//    frame, which is drained once it holds cap - 32 parents (16 in count
+//    frames of 48, 32 in fill frames of 64) or its parent frame is exhausted.  Processing frames in order keeps the emitted matches in
 //    lexicographic order of edge ids (used by enumeration).
 //  * The last motif edge is never expanded: survivors are counted with
 //    __popc(ballot) and added to per-warp accumulators; per-root / per-chunk
@@ -144,19 +144,21 @@ __device__ __forceinline__ bool pair_after(const GraphView& g, int32_t u, int32_
 
 // ------------------------------------------------------------ frame access
 
-struct Frame {
+template <int CAP>
+struct FrameT {
+    using L = FrameLayout<CAP>;
     char* p;
-    __device__ int64_t& tprev(int s) const { return ((int64_t*)(p + F_TPREV))[s]; }
+    __device__ int64_t& tprev(int s) const { return ((int64_t*)(p + L::TPREV))[s]; }
     // window end t_root + delta, as its distance from tprev (SPAN_FAR: too far to hold)
-    __device__ uint32_t& tspan(int s) const { return ((uint32_t*)(p + F_TEND))[s]; }
-    __device__ uint32_t& beg(int s) const { return ((uint32_t*)(p + F_BEG))[s]; }
-    __device__ uint32_t& len(int s) const { return ((uint32_t*)(p + F_LEN))[s]; }
-    __device__ uint32_t& root(int s) const { return ((uint32_t*)(p + F_ROOT))[s]; }
-    __device__ int32_t& node(int j, int s) const { return ((int32_t*)(p + F_NODE))[j * FCAP + s]; }
+    __device__ uint32_t& tspan(int s) const { return ((uint32_t*)(p + L::TEND))[s]; }
+    __device__ uint32_t& beg(int s) const { return ((uint32_t*)(p + L::BEG))[s]; }
+    __device__ uint32_t& len(int s) const { return ((uint32_t*)(p + L::LEN))[s]; }
+    __device__ uint32_t& root(int s) const { return ((uint32_t*)(p + L::ROOT))[s]; }
+    __device__ int32_t& node(int j, int s) const { return ((int32_t*)(p + L::NODE))[j * CAP + s]; }
     // eids follow the nb node rows
-    __device__ int32_t& eid(int nb, int j, int s) const { return ((int32_t*)(p + F_NODE))[(nb + j) * FCAP + s]; }
+    __device__ int32_t& eid(int nb, int j, int s) const { return ((int32_t*)(p + L::NODE))[(nb + j) * CAP + s]; }
     // anti-edge attached-edge times, at byte offset `row_off` of the frame
-    __device__ int64_t& anti_t(int row_off, int a, int s) const { return ((int64_t*)(p + row_off))[a * FCAP + s]; }
+    __device__ int64_t& anti_t(int row_off, int a, int s) const { return ((int64_t*)(p + row_off))[a * CAP + s]; }
 };
 
 // ------------------------------------------------------------ per-warp state
@@ -174,6 +176,9 @@ template <int MODE, bool STATS, int FEAT>
 struct Search {
     static constexpr bool ANTI = (FEAT & FEAT_ANTI) != 0;   // anti-edge checks compiled in
     static constexpr bool LOOK = (FEAT & FEAT_LOOK) != 0;   // look-ahead checks compiled in
+    static constexpr int CAP = MODE == MODE_FILL ? FCAP_FILL : FCAP_COUNT;   // parents per frame
+    static constexpr uint32_t DESCEND = CAP - 32;   // a child frame this full is drained next
+    using Frame = FrameT<CAP>;
     const GraphView& g;
     const QueryDev* __restrict__ qs;
     Ctrl* ctrl;
@@ -668,7 +673,7 @@ struct Search {
                 if (Off(lvl) < T(lvl)) {
                     step(lvl);
                     setOff(lvl, Off(lvl) + 32);
-                    if (lvl < k - 1 && P(lvl + 1) >= 32) { ++lvl; begin_frame(lvl); }
+                    if (lvl < k - 1 && P(lvl + 1) >= DESCEND) { ++lvl; begin_frame(lvl); }
                 }
                 continue;
             }
@@ -742,7 +747,7 @@ struct Search {
                 }
                 __syncwarp();
                 setP(1, cp + __popc(kb));
-                if (cp + __popc(kb) >= 32) drain(1);
+                if (cp + __popc(kb) >= DESCEND) drain(1);
             }
         }
         if (flush_at_end && k > 1 && P(1) > 0) drain(1);

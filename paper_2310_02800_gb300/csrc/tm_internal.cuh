@@ -149,7 +149,13 @@ struct AntiPlan {
     int64_t delta;     // window [t(e_i), t(e_i) + delta]
 };
 
-constexpr int FCAP = 64;          // parents per frame (two per lane)
+// Parents per frame (at most two per lane).  A level is descended into once its
+// frame holds cap - 32 parents, so one more 32-wide step of its parent level
+// always fits.  Count frames hold 48 (descend at 16): the smaller shared
+// memory footprint leaves more of each SM's unified L1 / shared memory to L1;
+// fill frames carry edge ids and keep 64 (descend at 32).
+constexpr int FCAP_COUNT = 48;
+constexpr int FCAP_FILL = 64;
 
 struct Plan {
     int32_t k, n_nodes;
@@ -175,19 +181,25 @@ inline unsigned plan_features(const Plan& p) {
     return f;
 }
 
-// Frame field offsets (bytes, relative to frame start), FCAP entries each.
+// Frame field offsets (bytes, relative to frame start), CAP entries each.
 //   tprev i64, tend - tprev u32 (0xFFFFFFFF when it does not fit: t_root + delta is
 //   then rebuilt from the root edge), beg u32 (bits 31/30: list kind), len u32, root u32,
 //   node[nb] i32, eid[i] i32 (enumerate only), anti_t[n_anti] i64 (motifs with
 //   anti-edges: time of each anti-edge's attached edge once bound)
-constexpr int F_TPREV = 0;
-constexpr int F_TEND = F_TPREV + 8 * FCAP;
-constexpr int F_BEG = F_TEND + 4 * FCAP;
-constexpr int F_LEN = F_BEG + 4 * FCAP;
-constexpr int F_ROOT = F_LEN + 4 * FCAP;
-constexpr int F_NODE = F_ROOT + 4 * FCAP;
+template <int CAP>
+struct FrameLayout {
+    static constexpr int TPREV = 0;
+    static constexpr int TEND = TPREV + 8 * CAP;
+    static constexpr int BEG = TEND + 4 * CAP;
+    static constexpr int LEN = BEG + 4 * CAP;
+    static constexpr int ROOT = LEN + 4 * CAP;
+    static constexpr int NODE = ROOT + 4 * CAP;
+};
+// Count frames (no edge ids) or fill frames (edge ids of the bound edges).
 inline int frame_bytes(int nb, int level, bool with_eids, int n_anti = 0) {
-    return F_NODE + 4 * FCAP * (nb + (with_eids ? level : 0)) + 8 * FCAP * n_anti;
+    if (with_eids)
+        return FrameLayout<FCAP_FILL>::NODE + 4 * FCAP_FILL * (nb + level) + 8 * FCAP_FILL * n_anti;
+    return FrameLayout<FCAP_COUNT>::NODE + 4 * FCAP_COUNT * nb + 8 * FCAP_COUNT * n_anti;
 }
 constexpr int WARP_HDR = 128;      // per-warp header: level cursors
 
