@@ -287,7 +287,7 @@ tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len,
         if (s->chunk_cnt) cudaFree(s->chunk_cnt);
         if (s->scan_tmp) cudaFree(s->scan_tmp);
         s->chunk_cnt = nullptr; s->scan_tmp = nullptr; s->chunk_cap = 0;
-        tm_status st = dev_alloc((void**)&s->chunk_cnt, (chunks + 1) * 8);
+        tm_status st = dev_alloc((void**)&s->chunk_cnt, chunk_buf_bytes(chunks));
         if (st != TM_OK) return st;
         s->scan_tmp_bytes = scan_temp_bytes(chunks + 1);
         st = dev_alloc(&s->scan_tmp, s->scan_tmp_bytes);
@@ -386,7 +386,7 @@ static tm_status run_count(tm_graph* g, tm_query* q, uint64_t rb, uint64_t re, c
     TM_CUDA(cudaMemsetAsync(s.counters, 0, s.counters_len * 8, st));
     TM_CUDA(cudaMemsetAsync(s.ready, 0, s.task_cap, st));
     if (per_root && re > rb) TM_CUDA(cudaMemsetAsync(per_root, 0, (re - rb) * 8, st));
-    if (chunk_counts) TM_CUDA(cudaMemsetAsync(s.chunk_cnt, 0, (nch + 1) * 8, st));
+    if (chunk_counts) TM_CUDA(cudaMemsetAsync(s.chunk_cnt, 0, (nch + 2) * 8, st));   // counts + list length
     if (q->profile) TM_CUDA(cudaEventRecord(q->ev[0], st));
     r = launch_search(g, MODE_COUNT, s.qdev(), 1, q->plan.warp_smem, q->plan.tune.warps_per_block,
                       plan_features(q->plan), &s, st,
@@ -540,9 +540,13 @@ extern "C" tm_status tm_enumerate(tm_graph* g, tm_query* q, void* stream, int32_
     if (s != TM_OK) return s;
     Scratch& sc = q->scratch;
     const uint64_t nch = n_chunks(m, q->plan.tune.chunk_roots);
-    // pass 2: chunk offsets
+    // pass 2: chunk offsets, and the chunks the fill pass must search
     s = exclusive_scan_u64(sc.chunk_cnt, sc.chunk_cnt, nch + 1, sc.scan_tmp, st);
     if (s != TM_OK) return s;
+    if (cap > 0) {
+        s = list_chunks(sc.chunk_cnt, nch, cap, g->num_sms, st);
+        if (s != TM_OK) return s;
+    }
     s = read_back(sc, st, 1);
     if (s != TM_OK) return s;
     const uint64_t tot = sc.counters_host[0];
@@ -820,7 +824,7 @@ extern "C" tm_status tm_enumerate_batch(tm_graph* g, tm_query* const* qs, int nq
         // each query's own scratch holds its chunk counts, then their offsets
         tm_status r = scratch_reserve(&qs[j]->scratch, g->device, 1, 1, nch[j], 0);
         if (r != TM_OK) return r;
-        TM_CUDA(cudaMemsetAsync(qs[j]->scratch.chunk_cnt, 0, (nch[j] + 1) * 8, st));
+        TM_CUDA(cudaMemsetAsync(qs[j]->scratch.chunk_cnt, 0, (nch[j] + 2) * 8, st));   // counts + list length
     }
     // pass 1: per-chunk counts of every query, one persistent launch per occupancy group
     std::vector<int> order(nq);
@@ -859,11 +863,15 @@ extern "C" tm_status tm_enumerate_batch(tm_graph* g, tm_query* const* qs, int nq
         if (s != TM_OK) return s;
     }
     if (kernel_ms) TM_CUDA(cudaEventRecord(bc->ev[1], st));
-    // pass 2: chunk offsets
+    // pass 2: chunk offsets, and the chunks the fill pass must search
     for (int j = 0; j < nq; ++j) {
         s = exclusive_scan_u64(qs[j]->scratch.chunk_cnt, qs[j]->scratch.chunk_cnt, nch[j] + 1,
                                qs[j]->scratch.scan_tmp, st);
         if (s != TM_OK) return s;
+        if (caps[j] > 0) {
+            s = list_chunks(qs[j]->scratch.chunk_cnt, nch[j], caps[j], g->num_sms, st);
+            if (s != TM_OK) return s;
+        }
     }
     // pass 3: rows of the queries with room for some, written from each chunk's
     // offset on the device (chunks past the cap or without matches are skipped)

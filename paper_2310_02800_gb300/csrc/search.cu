@@ -831,21 +831,22 @@ struct Search {
                 use_query(j);
             }
             uint64_t lc = c - q->chunk_base;
-            uint64_t cr = (uint64_t)q->plan.tune.chunk_roots;
-            uint64_t r0 = q->root_begin + lc * cr;
-            uint64_t r1 = min(q->root_end, r0 + cr);
+            const uint64_t cr = (uint64_t)q->plan.tune.chunk_roots;
             if (MODE == MODE_FILL) {
-                out_base = q->chunk_off[lc];
-                out_local = 0;
-                // the count pass found no match rooted in this chunk: nothing to write
-                if (q->chunk_off[lc + 1] == out_base) continue;
-                if (out_base >= q->cap) {
-                    // offsets never decrease: skip the rest of this query's chunks
+                // claim index lc -> the lc-th listed chunk (one holding a match whose
+                // rows start below the cap); past the list's end the rest of this
+                // query is skipped
+                if (lc >= q->chunk_off[q->n_chunks + 1]) {
                     unsigned long long nxt = (j + 1 < nq) ? qs[j + 1].chunk_base : total_chunks;
                     if (lane == 0) atomicMax(&ctrl->next_chunk, nxt);
                     continue;
                 }
+                lc = ((const uint32_t*)(q->chunk_off + q->n_chunks + 2))[lc];
+                out_base = q->chunk_off[lc];
+                out_local = 0;
             }
+            const uint64_t r0 = q->root_begin + lc * cr;
+            const uint64_t r1 = min(q->root_end, r0 + cr);
             roots(r0, r1, MODE == MODE_FILL);
         }
         if (MODE == MODE_COUNT && qi >= 0 && k > 1 && P(1) > 0) drain(1);
@@ -894,6 +895,41 @@ __global__ void __maxnreg__(56) search_kernel(const __grid_constant__ GraphView 
 }
 
 }  // namespace
+
+namespace {
+
+// The chunks of an enumeration that hold a match and whose rows start below
+// the cap, from the scanned row offsets: their ids are appended (in no
+// particular order) after the offsets and the list length (zeroed by the
+// caller), for the fill pass to claim.
+__global__ void list_chunks_kernel(unsigned long long* buf, uint64_t nch, uint64_t cap) {
+    const unsigned long long* off = buf;
+    unsigned long long* n_list = buf + nch + 1;
+    uint32_t* list = (uint32_t*)(buf + nch + 2);
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nch; base += stride) {
+        const uint64_t c = base + lane;
+        const bool keep = c < nch && off[c + 1] > off[c] && off[c] < cap;
+        const unsigned b = __ballot_sync(FULL, keep);
+        if (!b) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(n_list, (unsigned long long)__popc(b));
+        at = __shfl_sync(FULL, at, 0);
+        if (keep) list[at + __popc(b & ((1u << lane) - 1u))] = (uint32_t)c;
+    }
+}
+
+}  // namespace
+
+tm_status list_chunks(unsigned long long* chunk_buf, uint64_t nch, uint64_t cap, int num_sms, cudaStream_t st) {
+    if (nch == 0) return TM_OK;
+    const uint64_t blocks = std::min<uint64_t>((nch + 255) / 256, (uint64_t)num_sms * 8);
+    list_chunks_kernel<<<(unsigned)blocks, 256, 0, st>>>(chunk_buf, nch, cap);
+    note_launches(1);
+    TM_CUDA(cudaGetLastError());
+    return TM_OK;
+}
 
 namespace {
 std::mutex g_cfg_mu;

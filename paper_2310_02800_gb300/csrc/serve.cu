@@ -104,7 +104,7 @@ namespace {
 uint64_t req_bytes(const tm_graph* g, const Plan& p, int enumerate, uint64_t cap) {
     if (!enumerate) return 0;
     uint64_t nch = ((uint64_t)g->v.m + p.tune.chunk_roots - 1) / (uint64_t)p.tune.chunk_roots;
-    return cap * (uint64_t)p.k * 4 + (nch + 1) * 8 + scan_temp_bytes(nch + 1);
+    return cap * (uint64_t)p.k * 4 + chunk_buf_bytes(nch) + scan_temp_bytes(nch + 1);
 }
 
 uint64_t cost_key(const Plan& p, int enumerate) {
@@ -140,9 +140,9 @@ tm_status launch_batch(tm_server* s, Slot& sl) {
         if (!q->enumerate) continue;
         q->nch = (m + q->plan.tune.chunk_roots - 1) / (uint64_t)q->plan.tune.chunk_roots;
         TM_CUDA(dev_malloc_async((void**)&q->match, std::max<uint64_t>(q->cap * q->plan.k * 4, 16), sl.st));
-        TM_CUDA(dev_malloc_async((void**)&q->chunk, (q->nch + 1) * 8, sl.st));
+        TM_CUDA(dev_malloc_async((void**)&q->chunk, chunk_buf_bytes(q->nch), sl.st));
         TM_CUDA(dev_malloc_async(&q->scan_tmp, scan_temp_bytes(q->nch + 1), sl.st));
-        TM_CUDA(cudaMemsetAsync(q->chunk, 0, (q->nch + 1) * 8, sl.st));
+        TM_CUDA(cudaMemsetAsync(q->chunk, 0, (q->nch + 2) * 8, sl.st));   // counts + list length
     }
     // count launch over every request of the batch
     Scratch& cs = sl.count_s;
@@ -185,6 +185,8 @@ tm_status launch_batch(tm_server* s, Slot& sl) {
     for (Req* q : sl.batch) {
         if (!q->enumerate) continue;
         r = exclusive_scan_u64(q->chunk, q->chunk, q->nch + 1, q->scan_tmp, sl.st);
+        if (r != TM_OK) return r;
+        r = list_chunks(q->chunk, q->nch, q->cap, g->num_sms, sl.st);
         if (r != TM_OK) return r;
         QueryDev* qd = fs.qdev_stage() + ne;
         memset(qd, 0, sizeof(QueryDev));

@@ -239,6 +239,14 @@ struct Ctrl {
 };
 static_assert(sizeof(Ctrl) == 384, "control block is three 128-byte lines");
 
+// Enumeration chunk buffer of a query with nch root chunks: nch + 1 per-chunk
+// match counts (scanned in place into row offsets by the caller), then the
+// number of chunks holding a match whose rows start below the cap, and those
+// chunks' ids (uint32, in no particular order; written by list_chunks after
+// the scan).  The fill pass searches only the listed chunks.  The count pass
+// needs the counts and the list length zeroed: the first (nch + 2) * 8 bytes.
+inline size_t chunk_buf_bytes(uint64_t nch) { return (size_t)(nch + 2) * 8 + (size_t)nch * 4; }
+
 struct QueryDev {                    // one query of a launch
     Plan plan;
     uint64_t root_begin, root_end;
@@ -246,8 +254,8 @@ struct QueryDev {                    // one query of a launch
     uint64_t chunk_base;             // first global chunk index of this query
     unsigned long long* total;       // device counter
     unsigned long long* per_root;    // nullable (indexed by root - root_begin)
-    unsigned long long* chunk_cnt;   // nullable (enumerate count pass)
-    const unsigned long long* chunk_off;  // enumerate fill: exclusive prefix of chunk_cnt (n_chunks + 1 entries)
+    unsigned long long* chunk_cnt;   // nullable (enumerate count pass): chunk buffer, counts + list
+    const unsigned long long* chunk_off;  // enumerate fill: chunk buffer, offsets + list
     int32_t* match_out;              // enumerate fill
     uint64_t cap;
     unsigned long long* work;        // nullable: tm_work counters (2 + 2*TM_MAX_EDGES + 1)
@@ -290,6 +298,9 @@ void query_plan(tm_query* q, Plan* out);
 // The graph a query was compiled for, and the motif it was compiled from.
 const tm_graph* query_graph(const tm_query* q);
 const tm_motif* query_motif(const tm_query* q);
+
+// List the chunks of a scanned chunk buffer that the fill pass must search.
+tm_status list_chunks(unsigned long long* chunk_buf, uint64_t nch, uint64_t cap, int num_sms, cudaStream_t st);
 
 tm_status scratch_reserve(Scratch* s, int device, int nq, uint64_t counters_len, uint64_t chunks,
                           uint64_t task_cap);
