@@ -532,28 +532,40 @@ def e2e_leg(args, g, queries, dev):
     # caller-owned row buffers, allocated once (as a user reuses them)
     outs = [torch.empty((CAP, mo.k), dtype=torch.int32, device=f"cuda:{dev}") for mo in queries]
     times, h2d, d2h = [], 0, 0
-    for rep in range(2 + max(1, min(args.steps, 3))):
+    phases = {"load": [], "enumerate_batch": [], "rows_to_host": [], "free": []}
+    # host-timed: the median of 5 steps after 2 untimed ones, so one stall of the host does not
+    # stand for the step
+    for rep in range(2 + 5):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gg = tmg.Graph.load(g.n_nodes, src, dst, t, device=dev)
+        t1 = time.perf_counter()
         qs = [gg.compile(mo) for mo in queries]
         nws, tots, _ = gg.enumerate_batch(qs, outs)
+        t2 = time.perf_counter()
         dbytes = 0
         for nw, out, mo in zip(nws, outs, queries):
             host_rows.view(-1)[: nw * mo.k].copy_(out[:nw].reshape(-1))
             dbytes += nw * mo.k * 4 + 8
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
         for q in qs:
             q.free()
         gg.free()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        t4 = time.perf_counter()
+        dt = t4 - t0
         if rep >= 2:
             times.append(dt)
+            for key, a, b in (("load", t0, t1), ("enumerate_batch", t1, t2), ("rows_to_host", t2, t3),
+                              ("free", t3, t4)):
+                phases[key].append(1000 * (b - a))
         d2h = dbytes
     h2d = g.n_edges * (4 + 4 + 8)
-    sec = float(np.mean(times))
+    sec = float(np.median(times))
     return {"value": len(queries) * g.n_edges / sec, "unit": "root-edges/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * sec,
+            "phases_ms": {k: round(float(np.median(v)), 3) for k, v in phases.items()},
             "includes": "host->device upload and GPU build of the graph, one tm_enumerate_batch over the 4 "
                         "queries (exact counts + rows), rows to host"}
 

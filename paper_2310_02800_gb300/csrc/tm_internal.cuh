@@ -95,6 +95,8 @@ struct tm_graph {
     int device = 0;
     tmg::GraphView v{};
     std::vector<void*> allocs;     // device buffers owned by the graph
+    char* slab = nullptr;          // the graph's columns, carved from one allocation
+    size_t slab_used = 0, slab_cap = 0;
     int32_t* perm = nullptr;       // device: edge id -> input index
     uint64_t device_bytes = 0;
     int num_sms = 0;
