@@ -247,6 +247,31 @@ def test_donation_on_a_hub(tmg):
             assert q.count() == want, (mo.name, d)
 
 
+def test_star_continuations_ties_and_donation(tmg):
+    """Stars search the same hub list at every level (out- and in-stars from one node): hub
+    lists with many equal timestamps (each level's window starts after every tie of the
+    previous edge), donation at every split depth, a gap bound on the last edge only;
+    counts, per-root counts and rows vs the oracle."""
+    rng = np.random.default_rng(17)
+    n, m = 2000, 40_000
+    hubs = rng.integers(0, n, 3)
+    src = np.where(rng.random(m) < 0.6, rng.choice(hubs, m), rng.integers(0, n, m)).astype(np.int32)
+    dst = np.where(rng.random(m) < 0.6, rng.choice(hubs, m), rng.integers(0, n, m)).astype(np.int32)
+    t = (rng.integers(0, 400_000, m) // 50 * 50).astype(np.int64)      # ~8,000 distinct times
+    og = oracle.Graph(n, src, dst, t)
+    gg = tmg.Graph.load(n, src, dst, t)
+    gapped = synth.out_star(4, 2000)
+    gapped.gaps = [2000, 2000, 600]
+    gapped.name = "outstar4_gap600"
+    for mo in (synth.out_star(3, 1000), synth.out_star(4, 1000), synth.in_star(4, 1000), gapped):
+        want = og.count(mo)
+        q = gg.compile(mo)
+        for d in (0, 1, 2, 3):
+            q.set_tuning(4, 64, d, 0)
+            assert q.count() == want, (mo.name, d)
+        check_query(tmg, gg, og, mo, per_root=True, enum_cap=min(want, 200_000))
+
+
 def test_edge_cases(tmg):
     # empty graph
     gg = tmg.Graph.load(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
