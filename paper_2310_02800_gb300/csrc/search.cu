@@ -34,6 +34,11 @@
 //    graph edge must join their images later in the root's window; the
 //    pair-ordered out-list answers that with two searches, and partial
 //    matches without one are dropped before their subtrees are searched.
+//  * Enumeration is two launches of this kernel: a count launch leaves
+//    per-chunk match counts, a device scan turns them into row offsets,
+//    list_chunks_kernel lists the chunks holding a match below the cap, and a fill
+//    launch searches only the listed chunks again, each writing its rows in
+//    lexicographic order from its offset.
 //  * The kernel is instantiated per mode (count, enumeration fill), with or
 //    without work counters, and per feature set (anti-edges, look-ahead), so
 //    a plain motif runs code holding neither.
